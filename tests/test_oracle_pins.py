@@ -1,0 +1,401 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these checks re-types an oracle formula: each compares the oracle with an
+independent route (a definition built as a dense matrix, a closed form, a published
+test vector, an optimality condition, a second solver written here).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1809_04195_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------------
+# helpers built from definitions, independent of the oracle's numpy.fft route
+# ----------------------------------------------------------------------------------
+def centred_dft_matrix(n):
+    """D[k, j] = exp(-2 pi i (k - n/2)(j - n/2) / n) / sqrt(n): the centred unitary DFT
+    written from its definition (image and k-space origins at index n/2)."""
+    k = np.arange(n)[:, None] - n // 2
+    j = np.arange(n)[None, :] - n // 2
+    return np.exp(-2j * np.pi * k * j / n) / np.sqrt(n)
+
+
+def dense_A(maps, mask, phi):
+    """Dense matrix of A = P F S Phi (Eq. 5) on vec(alpha[M][K][Ny][Nz]) ->
+    vec(y[C][T][Ny][Nz]), assembled from Kronecker products of the definitions."""
+    C, M, Ny, Nz = maps.shape
+    T, K = phi.shape
+    N = Ny * Nz
+    F = np.kron(centred_dft_matrix(Ny), centred_dft_matrix(Nz))  # acts on vec(img[Ny][Nz])
+    A = np.zeros((C * T * N, M * K * N), np.complex128)
+    for c in range(C):
+        for t in range(T):
+            P = np.diag(mask[t].ravel().astype(float))
+            for m in range(M):
+                S = np.diag(maps[c, m].ravel())
+                blk = P @ F @ S
+                for k in range(K):
+                    r0 = (c * T + t) * N
+                    c0 = (m * K + k) * N
+                    A[r0:r0 + N, c0:c0 + N] += phi[t, k] * blk
+    return A
+
+
+def tiny_problem(seed, Ny=8, Nz=8, C=2, T=6, K=2, M=1, frac=0.5):
+    rng = np.random.default_rng(seed)
+    phi = synth.t2_basis(T, K)
+    maps = synth.coil_maps(C, Ny, Nz, rng, M=M)
+    mask = (rng.random((T, Ny, Nz)) < frac).astype(np.uint8)
+    return phi, maps, mask, rng
+
+
+def crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ----------------------------------------------------------------------------------
+# shift generator
+# ----------------------------------------------------------------------------------
+def test_splitmix64_published_vectors():
+    n_checked = 0
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(v) for v in line.split()]
+            seed, n, ref = w[0], w[1], w[2:]
+            assert O.splitmix64(seed, n) == ref
+            n_checked += 1
+    assert n_checked >= 2
+
+
+def test_llr_shifts_range_and_split():
+    sh = O.llr_shifts(1809, 4000, 8)
+    assert sh.shape == (4000, 2) and sh.dtype == np.int64
+    assert sh.min() == 0 and sh.max() == 7
+    # both axes take every value, and they are not the same sequence
+    assert set(sh[:, 0]) == set(range(8)) and set(sh[:, 1]) == set(range(8))
+    assert np.mean(sh[:, 0] == sh[:, 1]) < 0.3
+    h = O.splitmix64(1809, 3)
+    assert sh[2, 0] == (h[2] & 0xFFFFFFFF) % 8 and sh[2, 1] == (h[2] >> 32) % 8
+
+
+# ----------------------------------------------------------------------------------
+# F: centred unitary DFT
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("ny,nz", [(8, 12), (12, 8), (48, 64), (64, 48), (160, 8), (6, 10)])
+def test_fft2c_matches_definition(ny, nz):
+    rng = np.random.default_rng(ny * 1000 + nz)
+    x = crandn(rng, 3, ny, nz)
+    ref = np.einsum("ab,sbc,dc->sad", centred_dft_matrix(ny), x, centred_dft_matrix(nz))
+    got = O.fft2c(x)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max() * 10
+    # unitary and inverse
+    assert np.allclose(np.linalg.norm(got), np.linalg.norm(x), rtol=1e-13)
+    assert np.abs(O.ifft2c(got) - x).max() < 1e-12
+
+
+def test_fft2c_centred_delta_and_constant():
+    ny, nz = 16, 12
+    d = np.zeros((ny, nz), complex)
+    d[ny // 2, nz // 2] = 1.0
+    assert np.allclose(O.fft2c(d), np.full((ny, nz), 1 / np.sqrt(ny * nz)), atol=1e-15)
+    k = O.fft2c(np.ones((ny, nz), complex))
+    ref = np.zeros((ny, nz))
+    ref[ny // 2, nz // 2] = np.sqrt(ny * nz)
+    assert np.allclose(k, ref, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------
+# forward model, adjoint, space-time kernel
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("M", [1, 2])
+def test_forward_and_normal_match_dense_matrix(M):
+    phi, maps, mask, rng = tiny_problem(11 + M, M=M)
+    A = dense_A(maps, mask, phi)
+    alpha = crandn(rng, M, 2, 8, 8)
+    y = O.forward(alpha, maps, mask, phi)
+    assert np.abs(y.ravel() - A @ alpha.ravel()).max() < 1e-12
+    yy = crandn(rng, 2, 6, 8, 8) * mask[None]
+    assert np.abs(O.adjoint(yy, maps, mask, phi).ravel() - A.conj().T @ yy.ravel()).max() < 1e-12
+    psi = O.space_time_kernel(mask, phi)
+    nrm = O.normal(alpha, maps, psi)
+    assert np.abs(nrm.ravel() - A.conj().T @ (A @ alpha.ravel())).max() < 1e-12
+
+
+def test_adjoint_identity_knee_like():
+    rng = np.random.default_rng(5)
+    T, K, C, M, ny, nz = 20, 4, 4, 2, 32, 24
+    phi = synth.t2_basis(T, K)
+    maps = synth.coil_maps(C, ny, nz, rng, M=M)
+    mask = synth.vd_masks(T, ny, nz, 0.2, rng)
+    x = crandn(rng, M, K, ny, nz)
+    y = crandn(rng, C, T, ny, nz)
+    lhs = np.vdot(y, O.forward(x, maps, mask, phi))
+    rhs = np.vdot(O.adjoint(y, maps, mask, phi), x)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_psi_is_identity_under_full_sampling():
+    phi = synth.t2_basis(40, 4)
+    assert np.allclose(phi.T @ phi, np.eye(4), atol=1e-13)
+    psi = O.space_time_kernel(np.ones((40, 6, 4), np.uint8), phi)
+    assert np.abs(psi - np.eye(4)[None, None]).max() < 1e-13
+
+
+def test_psi_real_symmetric_bounded():
+    rng = np.random.default_rng(3)
+    phi = synth.t2_basis(32, 4)
+    mask = synth.vd_masks(32, 16, 12, 0.1, rng)
+    psi = O.space_time_kernel(mask, phi)
+    assert psi.dtype == np.float64
+    assert np.abs(psi - np.swapaxes(psi, -1, -2)).max() == 0.0
+    ev = np.linalg.eigvalsh(psi)
+    assert ev.min() > -1e-13 and ev.max() < 1 + 1e-13
+    # a point no echo samples has Psi = 0; a point only echo t samples has phi_t phi_t^T
+    m = np.zeros((32, 2, 2), np.uint8)
+    m[5, 0, 1] = 1
+    p = O.space_time_kernel(m, phi)
+    assert np.all(p[1, :] == 0) and np.all(p[0, 0] == 0)
+    assert np.allclose(p[0, 1], np.outer(phi[5], phi[5]), atol=0)
+
+
+@pytest.mark.parametrize("M", [1, 2])
+def test_commutation_psi_path_equals_echo_path(M):
+    """Sec. IV.B: S^H F^H Psi F S == A^H A computed through every echo."""
+    rng = np.random.default_rng(21 + M)
+    T, K, C, ny, nz = 24, 4, 3, 16, 12
+    phi = synth.t2_basis(T, K)
+    maps = synth.coil_maps(C, ny, nz, rng, M=M)
+    mask = synth.vd_masks(T, ny, nz, 0.15, rng)
+    a = crandn(rng, M, K, ny, nz)
+    psi = O.space_time_kernel(mask, phi)
+    ref = O.normal_explicit(a, maps, mask, phi)
+    assert np.abs(O.normal(a, maps, psi) - ref).max() <= 1e-12 * np.abs(ref).max()
+    # the same commutation for the data side: A^H y == S^H F^H (Phi^T P y)
+    y = crandn(rng, C, T, ny, nz)
+    r1 = O.adjoint(y, maps, mask, phi)
+    r2 = O.adjoint_projected(O.project(y, mask, phi), maps)
+    assert np.abs(r1 - r2).max() <= 1e-12 * np.abs(r1).max()
+
+
+def test_lipschitz_bounds_normal_operator():
+    for M in (1, 2):
+        phi, maps, mask, rng = tiny_problem(40 + M, M=M)
+        A = dense_A(maps, mask, phi)
+        lmax = np.linalg.eigvalsh(A.conj().T @ A).max()
+        L = O.lipschitz(maps, O.space_time_kernel(mask, phi))
+        assert lmax <= L * (1 + 1e-12)
+    # full sampling, maps normalised: L = ||A^H A|| = 1
+    phi, maps, _, _ = tiny_problem(50)
+    full = np.ones((6, 8, 8), np.uint8)
+    A = dense_A(maps, full, phi)
+    L = O.lipschitz(maps, O.space_time_kernel(full, phi))
+    assert abs(L - 1.0) < 1e-12
+    assert abs(np.linalg.eigvalsh(A.conj().T @ A).max() - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------------
+# singular value soft threshold and the LLR block grid
+# ----------------------------------------------------------------------------------
+def test_svt_closed_forms():
+    rng = np.random.default_rng(7)
+    X = crandn(rng, 64, 4)
+    s = np.linalg.svd(X, compute_uv=False)
+    assert np.abs(O.svt(X, 0.0) - X).max() < 1e-12
+    assert np.abs(O.svt(X, s[0] * 1.0001)).max() == 0.0
+    # rank one: sigma u v^H -> (sigma - tau)+ u v^H
+    u = crandn(rng, 64); u /= np.linalg.norm(u)
+    v = crandn(rng, 4); v /= np.linalg.norm(v)
+    R1 = 3.0 * np.outer(u, v.conj())
+    assert np.abs(O.svt(R1, 1.0) - 2.0 * np.outer(u, v.conj())).max() < 1e-12
+    # orthogonal columns with norms d: the thresholds act column by column
+    Q, _ = np.linalg.qr(crandn(rng, 64, 4))
+    d = np.array([5.0, 2.0, 0.7, 0.1])
+    out = O.svt(Q * d, 0.5)
+    assert np.abs(out - Q * np.maximum(d - 0.5, 0)).max() < 1e-12
+    # degenerate singular values: result independent of the basis chosen inside
+    Xd = Q * np.array([2.0, 2.0, 2.0, 1.0])
+    assert np.abs(O.svt(Xd, 0.5) - Q * np.array([1.5, 1.5, 1.5, 0.5])).max() < 1e-12
+
+
+def test_svt_is_the_nuclear_norm_prox():
+    """Optimality: the prox minimises 1/2||Z - X||^2 + tau ||Z||_*; random
+    perturbations never lower that cost."""
+    rng = np.random.default_rng(8)
+    X = crandn(rng, 16, 4)
+    tau = 1.3
+    Z = O.svt(X, tau)
+
+    def cost(W):
+        return 0.5 * np.linalg.norm(W - X) ** 2 + tau * np.linalg.svd(W, compute_uv=False).sum()
+
+    c0 = cost(Z)
+    for _ in range(200):
+        d = crandn(rng, 16, 4) * 10 ** rng.uniform(-4, -1)
+        assert cost(Z + d) >= c0 - 1e-12
+
+
+def _block_pixels(Ny, Nz, b, sy, sz, i, j):
+    """Pixels of block (i, j) for shift (sy, sz), straight from the grid definition."""
+    rows = [(sy + i * b + r) % Ny for r in range(b) if i * b + r < Ny]
+    cols = [(sz + j * b + c) % Nz for c in range(b) if j * b + c < Nz]
+    return rows, cols
+
+
+@pytest.mark.parametrize("Ny,Nz,b,sy,sz", [(16, 16, 8, 3, 5), (20, 12, 8, 7, 1), (12, 20, 6, 0, 5), (13, 9, 4, 2, 3)])
+def test_llr_prox_acts_on_the_shifted_blocks(Ny, Nz, b, sy, sz):
+    rng = np.random.default_rng(Ny + Nz + b)
+    K, M = 4, 1
+    nby, nbz = -(-Ny // b), -(-Nz // b)
+    for (i, j) in [(0, 0), (nby - 1, nbz - 1), (nby // 2, 0)]:
+        rows, cols = _block_pixels(Ny, Nz, b, sy, sz, i, j)
+        alpha = np.zeros((M, K, Ny, Nz), complex)
+        u = crandn(rng, len(rows), len(cols))
+        u /= np.linalg.norm(u)
+        v = crandn(rng, K)
+        v /= np.linalg.norm(v)
+        for a, r in enumerate(rows):
+            for c_, cc in enumerate(cols):
+                alpha[0, :, r, cc] = 4.0 * u[a, c_] * v  # rank-1 block, sigma = 4
+        out = O.llr_prox(alpha, b, 1.5, sy, sz)
+        assert np.abs(out - alpha * (2.5 / 4.0)).max() < 1e-12
+    # tau = 0 is the identity; a large tau clears everything
+    a = crandn(rng, M, K, Ny, Nz)
+    assert np.abs(O.llr_prox(a, b, 0.0, sy, sz) - a).max() < 1e-12
+    assert np.abs(O.llr_prox(a, b, 1e6, sy, sz)).max() == 0.0
+
+
+def test_llr_prox_is_block_separable_and_per_map():
+    rng = np.random.default_rng(99)
+    M, K, Ny, Nz, b, sy, sz = 2, 4, 16, 16, 8, 6, 2
+    a = crandn(rng, M, K, Ny, Nz)
+    out = O.llr_prox(a, b, 2.0, sy, sz)
+    rows, cols = _block_pixels(Ny, Nz, b, sy, sz, 1, 0)
+    a2 = a.copy()
+    # change a pixel outside block (1, 0) and map set 1 inside it
+    orow = [r for r in range(Ny) if r not in rows][0]
+    a2[0, :, orow, cols[0]] += 5.0
+    a2[1, :, rows[0], cols[0]] += 5.0
+    out2 = O.llr_prox(a2, b, 2.0, sy, sz)
+    idx = np.ix_(rows, cols)
+    assert np.abs(out2[0][:, idx[0], idx[1]] - out[0][:, idx[0], idx[1]]).max() < 1e-12
+    # each map set's block is the SVT of its own (pixels x K) matrix
+    X = a[1][:, idx[0], idx[1]].reshape(K, -1).T
+    ref = O.svt(X, 2.0).T.reshape(K, len(rows), len(cols))
+    assert np.abs(out[1][:, idx[0], idx[1]] - ref).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------------
+# FISTA
+# ----------------------------------------------------------------------------------
+def test_exact_recovery_full_sampling():
+    """Noiseless, fully sampled, lambda = 0, sum_c |S_c|^2 = 1: x_1 = alpha_true (mu = 1)."""
+    rng = np.random.default_rng(1)
+    T, K, C, ny, nz = 16, 4, 4, 16, 12
+    phi = synth.t2_basis(T, K)
+    maps = synth.coil_maps(C, ny, nz, rng)
+    full = np.ones((T, ny, nz), np.uint8)
+    a_true = crandn(rng, 1, K, ny, nz)
+    y = O.forward(a_true, maps, full, phi)
+    x, mu, trace = O.fista(y, "te", maps, full, phi, lam=0.0, b=4, iters=5, seed=3, return_trace=True)
+    assert abs(mu - 1.0) < 1e-12
+    for xi in trace:
+        assert np.abs(xi - a_true).max() < 1e-12
+    # a phantom outside the subspace gives its projection Phi^T x
+    xt = crandn(rng, 1, T, ny, nz)
+    y2 = O.sense_forward(xt, maps, full)
+    x2 = O.fista(y2, "te", maps, full, phi, lam=0.0, b=4, iters=2, seed=3)
+    assert np.abs(x2 - np.einsum("tk,mtyz->mkyz", phi, xt)).max() < 1e-12
+
+
+def test_fista_lambda0_converges_to_least_squares():
+    phi, maps, mask, rng = tiny_problem(77, frac=0.7)
+    A = dense_A(maps, mask, phi)
+    assert np.linalg.matrix_rank(A) == A.shape[1]
+    a_true = crandn(rng, 1, 2, 8, 8)
+    y = (A @ a_true.ravel()).reshape(2, 6, 8, 8) + 0.05 * crandn(rng, 2, 6, 8, 8) * mask[None]
+    ls = np.linalg.lstsq(A, y.ravel(), rcond=None)[0]
+    x = O.fista(y, "te", maps, mask, phi, lam=0.0, b=4, iters=3000, seed=0)
+    assert np.abs(x.ravel() - ls).max() < 1e-8
+
+
+def test_fista_no_shift_reaches_the_convex_minimiser():
+    """Shifts off: Eq. 5 is convex with one fixed block grid.  A proximal-gradient
+    (ISTA) run written here on the dense matrix, with an SVT built from numpy's SVD per
+    block, reaches the same minimiser and cost."""
+    phi, maps, mask, rng = tiny_problem(78, frac=0.7)
+    A = dense_A(maps, mask, phi)
+    a_true = crandn(rng, 1, 2, 8, 8)
+    y = (A @ a_true.ravel()).reshape(2, 6, 8, 8) + 0.1 * crandn(rng, 2, 6, 8, 8) * mask[None]
+    lam, b = 0.3, 4
+    x = O.fista(y, "te", maps, mask, phi, lam=lam, b=b, iters=2000, seed=0, shifts=False)
+
+    L = np.linalg.eigvalsh(A.conj().T @ A).max()
+    AhA = A.conj().T @ A
+    Ahy = A.conj().T @ y.ravel()
+    w = np.zeros(A.shape[1], complex)
+    for _ in range(6000):
+        g = (w - (AhA @ w - Ahy) / L).reshape(2, 8, 8)
+        for y0 in range(0, 8, b):
+            for z0 in range(0, 8, b):
+                X = g[:, y0:y0 + b, z0:z0 + b].reshape(2, -1).T
+                U, s, Vh = np.linalg.svd(X, full_matrices=False)
+                g[:, y0:y0 + b, z0:z0 + b] = ((U * np.maximum(s - lam / L, 0)) @ Vh).T.reshape(2, b, b)
+        w = g.ravel()
+    f_ista = O.objective(w.reshape(1, 2, 8, 8), y, maps, mask, phi, lam, b)
+    f_fista = O.objective(x, y, maps, mask, phi, lam, b)
+    assert abs(f_fista - f_ista) <= 1e-9 * abs(f_ista)
+    assert np.abs(x.ravel() - w).max() < 1e-6
+    # fixed point of the prox-gradient map
+    mu = 1.0 / O.lipschitz(maps, O.space_time_kernel(mask, phi))
+    g = x - mu * (O.normal(x, maps, O.space_time_kernel(mask, phi)) - O.adjoint(y, maps, mask, phi))
+    assert np.abs(O.llr_prox(g, b, mu * lam, 0, 0) - x).max() < 1e-8
+
+
+def test_fista_momentum_sequence():
+    """t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 with t_0 = 1: check the second iterate on a
+    problem where the gradient step is the identity map onto a_true (full sampling,
+    lambda = 0), so z_1 = x_1 and x_2 = x_1: momentum only scales a zero difference."""
+    rng = np.random.default_rng(2)
+    phi = synth.t2_basis(8, 2)
+    maps = synth.coil_maps(2, 8, 8, rng)
+    mask = np.ones((8, 8, 8), np.uint8)
+    mask[:, ::2, 1::3] = 0  # partial sampling: gradient step is not exact any more
+    a_true = crandn(rng, 1, 2, 8, 8)
+    y = O.forward(a_true, maps, mask, phi)
+    x, mu, tr = O.fista(y, "te", maps, mask, phi, lam=0.0, b=4, iters=3, seed=0, step=1.0, return_trace=True)
+    psi = O.space_time_kernel(mask, phi)
+    aty = O.adjoint(y, maps, mask, phi)
+    x1 = aty  # from x0 = z0 = 0
+    t1 = (1 + np.sqrt(5)) / 2
+    z1 = x1 + ((1 - 1) / t1) * x1
+    x2 = z1 - (O.normal(z1, maps, psi) - aty)
+    t2 = (1 + np.sqrt(1 + 4 * t1 * t1)) / 2
+    z2 = x2 + ((t1 - 1) / t2) * (x2 - x1)
+    x3 = z2 - (O.normal(z2, maps, psi) - aty)
+    assert np.abs(tr[0] - x1).max() < 1e-13
+    assert np.abs(tr[1] - x2).max() < 1e-13
+    assert np.abs(tr[2] - x3).max() < 1e-13
+
+
+def test_fista_rate_bound_beck_teboulle():
+    """Beck & Teboulle (2009, Thm 4.4): F(x_k) - F* <= 2 L ||x_0 - x*||^2 / (k + 1)^2.
+    Checked at lambda = 0 (F* from least squares) on an ill-conditioned tiny problem."""
+    phi, maps, mask, rng = tiny_problem(80, frac=0.45)
+    A = dense_A(maps, mask, phi)
+    y = crandn(rng, 2, 6, 8, 8) * mask[None]
+    ls = np.linalg.lstsq(A, y.ravel(), rcond=None)[0]
+    fstar = 0.5 * np.linalg.norm(A @ ls - y.ravel()) ** 2
+    L = O.lipschitz(maps, O.space_time_kernel(mask, phi))
+    _, mu, tr = O.fista(y, "te", maps, mask, phi, lam=0.0, b=4, iters=200, seed=0, return_trace=True)
+    R2 = np.linalg.norm(ls) ** 2
+    for k in (1, 5, 20, 50, 100, 200):
+        fk = 0.5 * np.linalg.norm(A @ tr[k - 1].ravel() - y.ravel()) ** 2
+        assert fk - fstar <= 2 * L * R2 / (k + 1) ** 2 + 1e-12
