@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the T2 Shuffling PICS solve (one GB300 per rank).
+
+One step = one whole reconstruction of the synthetic knee scan: t2sh_plan (maps,
+space-time kernel Psi, step, shifts) + t2sh_solve (A^H y, then 100 FISTA iterations of
+normal operator + LLR prox over all 320 slices of 256 x 160, C = 12, T = 80, K = 4,
+5 %/echo, lambda = 0.005, b = 8) + t2sh_destroy.  Inputs are device resident when the
+timed region starts (the `e2e` figure repeats it through host buffers).  The metric is
+slice-iterations per second (slices x iterations / seconds) over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank reconstructs its own copy of the scan (slices are independent
+problems: weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slice-iterations/s (T2 Shuffling FISTA PICS solve, full scan)"
+UNIT = "slice-iter/s"
+KERNEL_FILES = ["t2sh_device.cuh", "t2sh_plan.h", "k_fft.cu", "k_llr.cu", "k_prep.cu", "t2sh_api.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--slices", type=int, default=None, help="fewer slices (profiling runs only)")
+    ap.add_argument("--iters", type=int, default=None, help="fewer iterations (profiling runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import t2sh_synth as synth
+    sh = synth.KNEE_320x256x160
+    S = args.slices or sh.nslices
+    iters = args.iters if args.iters is not None else sh.iters
+    return sh, S, iters
+
+
+def config_dict(sh, S, iters, n):
+    return {"workload": f"synthetic knee scan, {S} slices of {sh.ny}x{sh.nz}, C={sh.ncoils}, T={sh.nechoes}, "
+                        f"K={sh.nbasis}, {int(sh.frac * 100)}%/echo, b={sh.block}, lambda={sh.lam}, "
+                        f"{iters} FISTA iterations, fp32",
+            "slices": S, "ny": sh.ny, "nz": sh.nz, "coils": sh.ncoils, "echoes": sh.nechoes, "basis": sh.nbasis,
+            "iterations": iters, "block": sh.block, "lambda": sh.lam, "parallelism": f"slices, dp{n}",
+            "l2": "inputs larger than L2 (per-iteration working set > 6 GB)"}
+
+
+# ------------------------------------------------------------------------------------
+# CPU legs: the FP64 oracle on a bounded sample (one slice, a few iterations)
+# ------------------------------------------------------------------------------------
+def oracle_sample(sh, iters):
+    """Run the oracle's FISTA on the central slice; returns (seconds, iterations)."""
+    import oracle as O
+    from oracle.acquire import proj_scan
+    centre = sh.nslices // 2
+    phi, mask, maps, ytil = proj_scan(sh, [centre])
+    t0 = time.perf_counter()
+    O.fista(ytil[0], "proj", maps[0], mask, phi, sh.lam, sh.block, iters, sh.seed)
+    return time.perf_counter() - t0, iters
+
+
+def cpu_baseline(sh):
+    """Oracle timing in a child process pinned to one BLAS thread."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench, t2sh_synth as s; "
+            "t, n = bench.oracle_sample(s.KNEE_320x256x160, 30); print(json.dumps([t, n]))") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    t, n = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"central slice (1 of {sh.nslices}) x {n} FISTA iterations, FP64 numpy oracle, "
+                      f"{t:.1f} s, 1 BLAS thread"}
+
+
+def run_reference(args):
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sh, S, iters = workload(args)
+    per_step = 8
+    for _ in range(args.warmup):
+        oracle_sample(sh, per_step)
+    tot, n = 0.0, 0
+    for _ in range(args.steps):
+        t, k = oracle_sample(sh, per_step)
+        tot += t
+        n += k
+    v = n / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(sh, S, iters, args.gpus),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: central slice x {per_step} FISTA iterations, FP64 numpy "
+                                       f"oracle, 1 BLAS thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------
+# GPU leg
+# ------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = []
+        for ln in (self.out or "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        sm = sorted(r[0] for r in load)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(load), "power_w_max": pmax}
+
+
+def algorithmic_bytes(S, C, M, K, N):
+    """Bytes one launch of each kernel class must move (complex64 = 8 B)."""
+    vec = S * M * K * N * 8
+    t = S * C * K * N * 8
+    maps = S * C * M * N * 8
+    return {"row_fwd": vec + maps + t, "row_adj": t + maps + vec, "col": 2 * t, "llr": 6 * vec}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_sha1():
+    h = hashlib.sha1()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_1809_04195_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per full-size launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_sha1") != kernel_source_sha1():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def make_inputs(sh, S, torch, t2sh, dev):
+    """Device-resident synthetic scan: phi, mask, maps [S][C][1][ny][nz], projected k-space
+    ytil [S][C][K][ny][nz] = Phi^T P (F S Phi alpha_true + w), scaled to max |ytil| = 1."""
+    import numpy as np
+    import t2sh_synth as synth
+    phi, mask, te = synth.scan_common(sh)
+    vol = synth.EllipsoidVolume.draw(synth.rng_for(sh.seed, 4, 0))
+    N = sh.ny * sh.nz
+    maps = torch.empty((S, sh.ncoils, 1, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    alpha = torch.empty((S, 1, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    for s in range(S):
+        st = synth.slice_structure(sh, s, volume=vol)
+        xt = synth.decay_series(st.rho, st.t2, te)
+        a = np.einsum("tk,tyz->kyz", phi, xt)
+        maps[s] = torch.from_numpy(st.maps.astype(np.complex64)).to(dev)
+        alpha[s, 0] = torch.from_numpy(a.astype(np.complex64)).to(dev)
+    phi_d = torch.from_numpy(phi.astype(np.float32)).to(dev)
+    mask_d = torch.from_numpy(mask).to(dev)
+    d = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S)
+    with t2sh.Plan(d, phi_d, mask_d, maps) as p:
+        ytil = p.forward(alpha, t2sh.KSPACE_PROJ)
+    # sigma = 1 % of the largest echo-0 sample of the central slice
+    c = min(S - 1, S // 2)
+    d1 = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=1)
+    with t2sh.Plan(d1, phi_d, mask_d, maps[c:c + 1].contiguous()) as p:
+        sig = 0.01 * float(p.forward(alpha[c:c + 1].contiguous(), t2sh.KSPACE_TE)[:, :, 0].abs().max())
+    # projected noise Phi^T P w, w ~ CN(0, sigma^2) per echo, drawn echo by echo
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(sh.seed)
+    mk = mask_d.to(torch.float32).reshape(sh.nechoes, 1, 1, N)
+    for s0 in range(0, S, 8):
+        s1 = min(S, s0 + 8)
+        acc = torch.zeros((s1 - s0, sh.ncoils, sh.nbasis, N), dtype=torch.complex64, device=dev)
+        for t in range(sh.nechoes):
+            w = torch.randn((s1 - s0, sh.ncoils, 1, N), dtype=torch.complex64, device=dev, generator=gen)
+            acc += (sig * w * mk[t]) * phi_d[t].reshape(1, 1, sh.nbasis, 1)
+        ytil[s0:s1] += acc.reshape(s1 - s0, sh.ncoils, sh.nbasis, sh.ny, sh.nz)
+    ytil /= ytil.abs().max()
+    del alpha
+    return phi_d, mask_d, maps, ytil
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1809_04195_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1809_04195_gb300 import t2sh
+
+    sh, S, iters = workload(args)
+    phi_d, mask_d, maps_d, ytil_d = make_inputs(sh, S, torch, t2sh, dev)
+    out_d = torch.empty((S, 1, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    dims = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, block=sh.block,
+                          lam=sh.lam, iters=iters, seed=sh.seed)
+    N = sh.ny * sh.nz
+    units = S * iters
+
+    def step(timing):
+        p = t2sh.Plan(dims, phi_d, mask_d, maps_d)
+        if timing:
+            p.timing(True)
+        p.solve(ytil_d, t2sh.KSPACE_PROJ, out=out_d)
+        tm = p.timing_read() if timing else None
+        p.close()
+        return tm
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    totals = {}
+    with Clocks(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            tm = step(True)
+            for k, (n, ms) in tm.items():
+                a = totals.setdefault(k, [0, 0.0])
+                a[0] += n
+                a[1] += ms
+        t1.record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * units * args.steps / (ms / 1000.0)
+
+    # e2e: the same reconstruction through host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        hphi = phi_d.cpu().numpy()
+        hmask = mask_d.cpu().numpy()
+        hmaps = maps_d.cpu().pin_memory()
+        hy = ytil_d.cpu().pin_memory()
+        hout = torch.empty(out_d.shape, dtype=torch.complex64).pin_memory()
+        hd = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, block=sh.block,
+                            lam=sh.lam, iters=iters, seed=sh.seed, flags=t2sh.HOST_IO)
+
+        def hstep():
+            p = t2sh.Plan(hd, hphi, hmask, hmaps)
+            p.solve(hy, t2sh.KSPACE_PROJ, out=hout)
+            p.close()
+
+        hstep()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        torch.cuda.synchronize()
+        es = time.perf_counter() - e0
+        if world > 1:
+            tt = torch.tensor([es], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            es = float(tt.item())
+        h2d = hphi.nbytes + hmask.nbytes + hmaps.numel() * 8 + hy.numel() * 8
+        e2e = {"value": world * units * args.steps / es, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(hout.numel() * 8), "full_scan_s": es / args.steps,
+               "api": "t2sh_plan + t2sh_solve with T2SH_HOST_IO (pinned host buffers)"}
+        del hmaps, hy, hout
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, src = measured_peaks()
+    ab = algorithmic_bytes(S, sh.ncoils, 1, sh.nbasis, N)
+    kern = {k: {"launches": n, "ms_total": m, "ms_per_launch": (m / n if n else None),
+                "algorithmic_bytes_per_launch": ab.get(k)} for k, (n, m) in totals.items() if n}
+    dom = max((k for k in kern if k in ab), key=lambda k: kern[k]["ms_total"])
+    avg_s = kern[dom]["ms_per_launch"] / 1000.0
+    achieved = ab[dom] / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": src, "traffic": ncu_traffic(dom),
+            "algorithmic_bytes_per_launch": ab[dom],
+            "per_kernel": {k: {**v, "achieved_gbs": (ab[k] / (v["ms_per_launch"] / 1000.0) / 1e9
+                                                     if k in ab and v["ms_per_launch"] else None)}
+                           for k, v in kern.items()}}
+    launches = sum(v["launches"] for v in kern.values()) + 2 * args.steps  # + maps/Psi kernels of t2sh_plan
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "full_scan_s": ms / args.steps / 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded 3D ellipsoid knee phantom, smooth coil maps, variable-density masks)",
+            "config": config_dict(sh, S, iters, world), "roofline": roof, "gpu_launches": launches,
+            "clocks": clk.summary(), "e2e": e2e}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sh)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * t2sh.h -- C ABI of the GB300 (sm_103a) T2 Shuffling PICS solver.
+ *
+ * The library solves, independently for every decoupled readout slice (Sec. II.A:
+ * after the inverse FFT along the fully sampled readout the 3D problem splits into 2D
+ * (ky, kz) problems), the T2 Shuffling reconstruction of Eq. 5:
+ *
+ *     argmin_alpha  1/2 || y - P F S Phi alpha ||_2^2  +  lambda sum_n || R_n(alpha) ||_*
+ *
+ * with FISTA (Sec. II.A, Sec. III.B).  The normal operator is applied through the
+ * space-time kernel Psi(n) = Phi^T P(n) Phi (Sec. IV.B) and the LLR prox is the
+ * singular-value soft threshold of non-overlapping b x b x K blocks of the randomly
+ * circular-shifted coefficient images (Eq. 4, Sec. IV.C).
+ *
+ * Conventions shared by every entry point
+ *   - Complex arrays are interleaved single precision (re, im), C order, last index
+ *     fastest.  Shapes below name their dimensions; S = nslices, C = ncoils,
+ *     M = nmaps, T = nechoes, K = nbasis.
+ *   - F is the centred, unitary 2D DFT over (ny, nz): k-space arrays hold DC at
+ *     (ny/2, nz/2), image arrays hold the image centre at (ny/2, nz/2).
+ *   - Array arguments are DEVICE pointers owned by the caller, unless the plan was
+ *     created with T2SH_HOST_IO, in which case the k-space, map, mask, basis and
+ *     result arguments of t2sh_plan / t2sh_solve are HOST pointers (pinned memory
+ *     recommended) and the library copies them through its own device buffers.
+ *     Device pointers must be 16-byte aligned.
+ *   - Work is enqueued on the plan's stream and is asynchronous unless stated.
+ *   - Errors are reported by status code only; nothing is thrown across the ABI.
+ *     t2sh_last_error() returns a message for the last failing call of the calling
+ *     thread.  A plan is not thread-safe: use one plan per host thread and stream.
+ */
+#ifndef T2SH_H
+#define T2SH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  T2SH_OK = 0,
+  T2SH_EINVAL = 1,       /* bad argument or unsupported dimension                      */
+  T2SH_ENOMEM = 2,       /* device allocation failed or the workspace cap was exceeded */
+  T2SH_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed                */
+  T2SH_EUNSUPPORTED = 4, /* valid request that this build does not implement          */
+  T2SH_ETIMEOUT = 5,     /* a bounded device wait ran out                              */
+  T2SH_EBUSY = 6         /* the plan is in use                                         */
+} t2sh_status;
+
+/* t2sh_dims.precision */
+enum { T2SH_FP32 = 0, T2SH_MIXED_BF16 = 1 };
+
+/* kform argument: layout of k-space data */
+enum {
+  T2SH_KSPACE_TE = 0,  /* zero-filled per-echo data      [S][C][T][ny][nz] complex */
+  T2SH_KSPACE_PROJ = 1 /* projected data Phi^T P y       [S][C][K][ny][nz] complex */
+};
+
+/* t2sh_dims.flags */
+#define T2SH_NO_SHIFT 0x1u /* LLR without random shifts (fixed block grid)            */
+#define T2SH_HOST_IO 0x2u  /* array arguments of plan/solve are host pointers         */
+
+typedef struct {
+  int32_t ny, nz;          /* slice matrix (phase encodes y, z); both even, 2/3/5-smooth,
+                              8 <= ny, nz <= 512                                          */
+  int32_t ncoils;          /* C >= 1 (virtual coils after compression, Sec. III.A)       */
+  int32_t nmaps;           /* M in {1, 2}: soft-SENSE map sets (Sec. II.A)               */
+  int32_t nechoes;         /* T >= K: echo train length                                  */
+  int32_t nbasis;          /* K in [1, 8]: subspace size (Eq. 3)                         */
+  int32_t nslices;         /* S >= 1: decoupled readout slices solved together           */
+  int32_t block;           /* LLR block edge b in [1, 16] (blocks b x b, Eq. 4)          */
+  float lambda;            /* LLR weight lambda >= 0 (Eq. 4)                             */
+  int32_t iters;           /* FISTA iterations >= 0                                      */
+  uint64_t seed;           /* seed of the random LLR shifts                              */
+  float step;              /* > 0: FISTA step mu; <= 0: the plan computes mu = 1/L with
+                              L = max_n lambda_max Psi(n) * max_p lambda_max S(p)^H S(p) */
+  int32_t precision;       /* T2SH_FP32 (T2SH_MIXED_BF16: reserved, T2SH_EUNSUPPORTED)   */
+  uint32_t flags;          /* T2SH_NO_SHIFT | T2SH_HOST_IO                                */
+} t2sh_dims;
+
+typedef struct t2sh_plan_s* t2sh_plan_t;
+
+/*
+ * t2sh_plan -- validate dims, allocate the plan's device workspace and precompute
+ * what every iteration shares (Sec. IV.B, Sec. IV.C "basis and space-time kernel
+ * caching"):
+ *   - Psi(n) = Phi^T P(n) Phi for every k-space point (real symmetric, upper triangle
+ *     stored, Sec. IV.B), built from mask and phi;
+ *   - the coil maps with the FFT centring sign (-1)^(y+z) folded in (Sec. IV.A);
+ *   - the LLR shift table of all iterations (t2sh_shifts);
+ *   - the step mu (dims.step, or 1/L as described above).
+ *
+ *   phi   [T][K]            float32, real temporal basis Phi (Eq. 3)
+ *   mask  [T][ny][nz]       uint8 one-zero sampling pattern per echo (centred k-space)
+ *   maps  [S][C][M][ny][nz] complex coil sensitivities S_{c,m} per slice
+ *   stream                  cudaStream_t the plan enqueues on (NULL: default stream)
+ *   out                     receives the plan handle; NULL on failure
+ *
+ * The inputs are copied; the caller may free them when t2sh_plan returns (it
+ * synchronises the stream once to read back mu).  Errors: EINVAL (dims, NULL
+ * pointers), ENOMEM (allocation), ECUDA.
+ */
+t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* mask,
+                      const void* maps, void* stream, t2sh_plan_t* out);
+
+/* Release every device buffer of the plan (after synchronising its stream). */
+t2sh_status t2sh_destroy(t2sh_plan_t plan);
+
+/*
+ * t2sh_forward -- y = A x = P F S Phi x (Eq. 5 forward model; Eq. 1 per echo).
+ *   x [S][M][K][ny][nz] complex (device)
+ *   y kform == T2SH_KSPACE_TE:   [S][C][T][ny][nz] zero-filled per-echo k-space
+ *     kform == T2SH_KSPACE_PROJ: [S][C][K][ny][nz] = Phi^T P A x = Psi (F S x)
+ * Device pointers only.  Errors: EINVAL.
+ */
+t2sh_status t2sh_forward(t2sh_plan_t plan, const void* x, void* y, int32_t kform);
+
+/*
+ * t2sh_adjoint -- x = A^H y = S^H F^H Phi^T P y (the data term of the FISTA
+ * gradient, Sec. II.A).  y as in t2sh_forward (a TE-form y is masked by P first);
+ * x [S][M][K][ny][nz].  Device pointers only.
+ */
+t2sh_status t2sh_adjoint(t2sh_plan_t plan, const void* y, int32_t kform, void* x);
+
+/*
+ * t2sh_normal_op -- y = A^H A x = S^H F^H Psi F S x (Sec. IV.B, Algorithm 1).
+ *   x, y [S][M][K][ny][nz] complex (device); x == y is allowed.
+ */
+t2sh_status t2sh_normal_op(t2sh_plan_t plan, const void* x, void* y);
+
+/*
+ * t2sh_llr_prox -- in place, x <- LLR prox of x with threshold tau (Eq. 4, Sec. IV.C):
+ * for every map set m and block (i, j) covering rows (sy + i b + r) mod ny and
+ * columns (sz + j b + c) mod nz (the last block per axis partial when b does not
+ * divide the size), the (pixels x K) matrix X becomes U max(Sigma - tau, 0) V^H.
+ *   x [S][M][K][ny][nz] complex (device); tau >= 0; 0 <= sy, sz < block.
+ */
+t2sh_status t2sh_llr_prox(t2sh_plan_t plan, void* x, float tau, int32_t sy, int32_t sz);
+
+/*
+ * t2sh_solve -- dims.iters FISTA iterations on Eq. 5 (Sec. II.A, Sec. III.B):
+ *   x_0 = z_0 = 0, t_0 = 1;  g = z_k - mu (A^H A z_k - A^H y);
+ *   x_{k+1} = LLR prox of g, threshold mu*lambda, shift of iteration k;
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2;  z_{k+1} = x_{k+1} + (t_k - 1)/t_{k+1} (x_{k+1} - x_k).
+ *   kspace     per kform (see above); a TE-form input is masked and projected first
+ *   alpha_out  [S][M][K][ny][nz] complex: x_iters
+ *   residual_out  NULL, or host double[iters]: ||x_{k+1} - x_k||_2 / ||x_{k+1}||_2 over
+ *              all slices; when non-NULL the call synchronises the stream.
+ * With T2SH_HOST_IO, kspace and alpha_out are host pointers and the call returns
+ * after alpha_out is written.
+ */
+t2sh_status t2sh_solve(t2sh_plan_t plan, const void* kspace, int32_t kform, void* alpha_out,
+                       double* residual_out);
+
+/* The step mu the plan uses (host float). */
+t2sh_status t2sh_get_step(t2sh_plan_t plan, float* step);
+
+/*
+ * t2sh_shifts -- host only: the LLR shift pair of every iteration, out[2*it] = sy,
+ * out[2*it+1] = sz, from output it+1 of SplitMix64(seed) (Steele, Lea, Flood 2014):
+ * sy = (low 32 bits) mod block, sz = (high 32 bits) mod block.  The paper only says
+ * the shift is random and smaller than the patch (Sec. IV.C); this is the library's
+ * generator.  out must hold 2*iters int32.
+ */
+t2sh_status t2sh_shifts(uint64_t seed, int32_t iters, int32_t block, int32_t* out);
+
+/* Host only: device bytes a plan with these dims allocates (for admission control). */
+t2sh_status t2sh_workspace_bytes(const t2sh_dims* dims, size_t* bytes);
+
+/*
+ * Kernel timing.  While enabled, the plan records a CUDA event pair on its stream
+ * around every kernel it launches and counts the launches, per kernel class:
+ *   0 row pass forward  (S.z then DFT along z)           1 row pass adjoint (IDFT_z, S^H, coil sum)
+ *   2 column pass       (DFT_y, Psi, IDFT_y or variants)  3 LLR prox / FISTA update
+ *   4 (reserved: plan-time kernels run inside t2sh_plan, before timing can be enabled)
+ *   5 projection of per-echo k-space
+ * t2sh_timing_enable(plan, 1) clears the counters and starts recording; (plan, 0) stops.
+ * t2sh_timing_read synchronises the stream and returns the launch count and the summed
+ * event-to-event milliseconds of one class since the last enable.  Recording adds two
+ * event records per launch; leave it off when not measuring.
+ */
+t2sh_status t2sh_timing_enable(t2sh_plan_t plan, int32_t enable);
+t2sh_status t2sh_timing_read(t2sh_plan_t plan, int32_t kernel_class, int64_t* launches, double* ms);
+
+/* Message of the last failing call on this thread ("" if none).  Never NULL. */
+const char* t2sh_last_error(void);
+
+/* ABI version: 100 * major + minor. */
+int32_t t2sh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* T2SH_H */

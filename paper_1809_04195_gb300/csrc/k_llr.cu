@@ -1,0 +1,200 @@
+// Locally-low-rank prox (Eq. 4, Sec. II.B) in one pass over the coefficient images,
+// as Sec. IV.C describes: the random circular shift is folded into the gather
+// indices (no shifted copy), each block is thresholded on chip and written back.
+//
+// One CTA per (slice, band of b shifted rows).  Per block (b x b pixels x K, per map
+// set) a warp forms the K x K Gram matrix G = X^H X with shuffle reductions; one
+// thread per block then eigendecomposes G = V diag(lambda) V^H in float64 (cyclic
+// Jacobi), sigma_i = sqrt(lambda_i), and forms W = V diag(max(1 - tau/sigma_i, 0)) V^H,
+// so that X W = U max(Sigma - tau, 0) V^H (since X V = U Sigma).  The FISTA variant
+// fuses the gradient step before the prox and the momentum update after it (Sec. II.A).
+#include "t2sh_device.cuh"
+
+namespace t2sh {
+
+template <int KC, bool FISTA>
+__global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x, float2* z,
+                                                const float2* __restrict__ grad, const float2* __restrict__ aty) {
+  extern __shared__ float2 smem[];
+  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, M = g.M, b = a.b;
+  const int s = blockIdx.y, band = blockIdx.x;
+  const int rb = min(b, ny - band * b);
+  const int nbz = (nz + b - 1) / b;
+  const int nblk = M * nbz;
+  float2* gs = smem;                                   // [M][K][rb][nz]
+  float2* wm = gs + (size_t)M * K * rb * nz;           // [nblk][KC][KC]
+  float* gram = reinterpret_cast<float*>(wm + (size_t)nblk * KC * KC);  // [nblk][KC*KC]
+
+  // 1. gather the band (gradient step fused for FISTA)
+  const int nel = M * K * rb * nz;
+  for (int e = threadIdx.x; e < nel; e += kThreads) {
+    const int zz = e % nz;
+    int rest = e / nz;
+    const int r = rest % rb;
+    rest /= rb;  // m * K + k
+    const int y = (a.sy + band * b + r) % ny;
+    const long long gi = ((long long)s * M * K + rest) * N + (long long)y * nz + zz;
+    float2 v;
+    if (FISTA) {
+      const float2 zv = z[gi], gv = grad[gi], av = aty[gi];
+      v = make_float2(zv.x - a.mu * (gv.x - av.x), zv.y - a.mu * (gv.y - av.y));
+    } else {
+      v = x[gi];
+    }
+    gs[e] = v;
+  }
+  __syncthreads();
+
+  // 2. Gram matrices, one warp per block
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int blk = warp; blk < nblk; blk += kThreads / 32) {
+    const int m = blk / nbz, j = blk - m * nbz;
+    const int cb = min(b, nz - j * b);
+    float gr[KC][KC];  // upper: re at [k][l] (k <= l), im at [l][k] (l > k)
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+#pragma unroll
+      for (int l = 0; l < KC; ++l) gr[k][l] = 0.f;
+    for (int p = lane; p < rb * cb; p += 32) {
+      const int r = p / cb, cc = p - r * cb;
+      const int zz = (a.sz + j * b + cc) % nz;
+      float2 xv[KC];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[((m * K + k) * rb + r) * nz + zz] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+#pragma unroll
+        for (int l = k; l < KC; ++l) {
+          // conj(x_k) x_l
+          gr[k][l] = fmaf(xv[k].x, xv[l].x, fmaf(xv[k].y, xv[l].y, gr[k][l]));
+          if (l > k) gr[l][k] = fmaf(xv[k].x, xv[l].y, fmaf(-xv[k].y, xv[l].x, gr[l][k]));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+#pragma unroll
+      for (int l = 0; l < KC; ++l)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gr[k][l] += __shfl_xor_sync(0xffffffffu, gr[k][l], o);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+#pragma unroll
+        for (int l = 0; l < KC; ++l) gram[blk * KC * KC + k * KC + l] = gr[k][l];
+    }
+  }
+  __syncthreads();
+
+  // 3. eigendecomposition and threshold weights, one thread per block
+  for (int blk = threadIdx.x; blk < nblk; blk += kThreads) {
+    double ar[KC][KC], ai[KC][KC], vr[KC][KC], vi[KC][KC];
+    const float* gp = gram + blk * KC * KC;
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+#pragma unroll
+      for (int l = 0; l < KC; ++l) {
+        if (k == l) { ar[k][l] = gp[k * KC + k]; ai[k][l] = 0.0; }
+        else if (k < l) { ar[k][l] = gp[k * KC + l]; ai[k][l] = gp[l * KC + k]; }
+        else { ar[k][l] = gp[l * KC + k]; ai[k][l] = -gp[k * KC + l]; }
+      }
+    herm_jacobi<double, KC>(ar, ai, vr, vi, 16);
+    double f[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      const double sig = sqrt(fmax(ar[i][i], 0.0));
+      f[i] = (sig > (double)a.tau) ? 1.0 - (double)a.tau / sig : 0.0;
+    }
+    float2* w = wm + (size_t)blk * KC * KC;
+#pragma unroll
+    for (int l = 0; l < KC; ++l)
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        // W_lk = sum_i V_li f_i conj(V_ki)
+        double wr = 0.0, wi = 0.0;
+#pragma unroll
+        for (int i = 0; i < KC; ++i) {
+          wr += f[i] * (vr[l][i] * vr[k][i] + vi[l][i] * vi[k][i]);
+          wi += f[i] * (vi[l][i] * vr[k][i] - vr[l][i] * vi[k][i]);
+        }
+        w[l * KC + k] = make_float2((float)wr, (float)wi);
+      }
+  }
+  __syncthreads();
+
+  // 4. X' = X W, then FISTA momentum; write back
+  double d2 = 0.0, x2 = 0.0;
+  const int npx = M * rb * nz;
+  for (int e = threadIdx.x; e < npx; e += kThreads) {
+    const int zz = e % nz;
+    const int rest = e / nz;
+    const int r = rest % rb, m = rest / rb;
+    const int y = (a.sy + band * b + r) % ny;
+    const int j = (((zz - a.sz) % nz + nz) % nz) / b;
+    const float2* w = wm + (size_t)(m * nbz + j) * KC * KC;
+    float2 xv[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[((m * K + k) * rb + r) * nz + zz] : make_float2(0.f, 0.f);
+    const long long gb = ((long long)(s * M + m) * K) * N + (long long)y * nz + zz;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (k < K) {
+        float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < KC; ++l) cfma(o, xv[l], w[l * KC + k]);
+        const long long gi = gb + (long long)k * N;
+        if (FISTA) {
+          const float2 xo = x[gi];
+          const float2 dx = csub(o, xo);
+          z[gi] = make_float2(o.x + a.beta * dx.x, o.y + a.beta * dx.y);
+          d2 += (double)dx.x * dx.x + (double)dx.y * dx.y;
+          x2 += (double)o.x * o.x + (double)o.y * o.y;
+        }
+        x[gi] = o;
+      }
+    }
+  }
+  if (FISTA && a.res != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    }
+    if (lane == 0) {
+      atomicAdd(a.res, d2);
+      atomicAdd(a.res + 1, x2);
+    }
+  }
+}
+
+template <int KC, bool FISTA>
+static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
+                          const float2* aty, cudaStream_t st) {
+  const int nbz = (g.nz + a.b - 1) / a.b;
+  const int nblk = g.M * nbz;
+  const size_t sm = sizeof(float2) * ((size_t)g.M * g.K * a.b * g.nz + (size_t)nblk * KC * KC) +
+                    sizeof(float) * (size_t)nblk * KC * KC;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_llr<KC, FISTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((g.ny + a.b - 1) / a.b, g.S);
+  k_llr<KC, FISTA><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
+                       const float2* aty, cudaStream_t st) {
+  const bool fista = (z != nullptr);
+  if (g.K <= 4) return fista ? llr_go<4, true>(g, a, x, z, grad, aty, st) : llr_go<4, false>(g, a, x, z, grad, aty, st);
+  return fista ? llr_go<8, true>(g, a, x, z, grad, aty, st) : llr_go<8, false>(g, a, x, z, grad, aty, st);
+}
+
+size_t llr_smem_bytes(const Geom& g, int b) {
+  const int kc = g.K <= 4 ? 4 : 8;
+  const int nblk = g.M * ((g.nz + b - 1) / b);
+  return sizeof(float2) * ((size_t)g.M * g.K * b * g.nz + (size_t)nblk * kc * kc) + sizeof(float) * (size_t)nblk * kc * kc;
+}
+
+}  // namespace t2sh

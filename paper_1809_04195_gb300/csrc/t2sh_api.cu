@@ -1,0 +1,510 @@
+// Host runtime behind the C ABI of include/t2sh.h: argument validation, the plan's
+// device workspace, plan-time precomputation (Psi, sign-folded maps, step, shift
+// table) and the FISTA driver that enqueues the kernels of each iteration.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/t2sh.h"
+#include "t2sh_plan.h"
+
+namespace t2sh {
+size_t llr_smem_bytes(const Geom& g, int b);
+}
+
+using namespace t2sh;
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+#define T2SH_CK(call)                                                                \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return T2SH_ECUDA;                                                             \
+    }                                                                                \
+  } while (0)
+
+#define T2SH_REQ(cond, ...)        \
+  do {                             \
+    if (!(cond)) {                 \
+      set_err(__VA_ARGS__);        \
+      return T2SH_EINVAL;          \
+    }                              \
+  } while (0)
+
+// SplitMix64 (Steele, Lea & Flood 2014): output number i+1 of the stream from `seed`.
+uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t zz = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  zz = (zz ^ (zz >> 30)) * 0xBF58476D1CE4E5B9ull;
+  zz = (zz ^ (zz >> 27)) * 0x94D049BB133111EBull;
+  return zz ^ (zz >> 31);
+}
+
+bool smooth235(int n) {
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+// Radix plan: as many radix-16 passes as divide n, then 8, 4, 2, 5, 3.
+bool make_fft_plan(int n, FftPlan& p) {
+  p.n = n;
+  p.npass = 0;
+  int m = n, ns = 1;
+  auto add = [&](int r) {
+    if (p.npass >= kMaxPass) return false;
+    p.radix[p.npass] = r;
+    p.ns[p.npass] = ns;
+    ns *= r;
+    m /= r;
+    ++p.npass;
+    return true;
+  };
+  while (m % 16 == 0)
+    if (!add(16)) return false;
+  for (int r : {8, 4, 2, 5, 3})
+    while (m % r == 0)
+      if (!add(r)) return false;
+  return m == 1;
+}
+
+size_t cbytes(long long n) { return (size_t)n * sizeof(float2); }
+
+struct Footprint {
+  size_t maps, psi, phi, mask, vec, t, tw, shifts, red;
+  size_t total() const { return maps + psi + phi + mask + 4 * vec + t + tw + shifts + red; }
+};
+
+Footprint footprint(const t2sh_dims& d) {
+  const long long N = (long long)d.ny * d.nz;
+  const int P = d.nbasis * (d.nbasis + 1) / 2;
+  Footprint f;
+  f.maps = cbytes((long long)d.nslices * d.ncoils * d.nmaps * N);
+  f.psi = sizeof(float) * P * N;
+  f.phi = sizeof(float) * d.nechoes * d.nbasis;
+  f.mask = (size_t)d.nechoes * N;
+  f.vec = cbytes((long long)d.nslices * d.nmaps * d.nbasis * N);
+  f.t = cbytes((long long)d.nslices * d.ncoils * d.nbasis * N);
+  f.tw = cbytes(d.ny + d.nz);
+  f.shifts = 0;
+  f.red = sizeof(double) * 2 * (size_t)(d.iters > 0 ? d.iters : 1) + 64;
+  return f;
+}
+
+t2sh_status validate(const t2sh_dims* d) {
+  T2SH_REQ(d != nullptr, "dims is NULL");
+  T2SH_REQ(d->ny >= 8 && d->nz >= 8 && d->ny <= 512 && d->nz <= 512, "ny, nz must be in [8, 512] (got %d, %d)",
+           d->ny, d->nz);
+  T2SH_REQ(d->ny % 2 == 0 && d->nz % 2 == 0, "ny, nz must be even (centred FFT)");
+  T2SH_REQ(smooth235(d->ny) && smooth235(d->nz), "ny, nz must be 2/3/5-smooth");
+  T2SH_REQ(d->ncoils >= 1 && d->ncoils <= 1024, "ncoils out of range");
+  T2SH_REQ(d->nmaps >= 1 && d->nmaps <= kMaxM, "nmaps must be 1 or 2");
+  T2SH_REQ(d->nbasis >= 1 && d->nbasis <= kMaxK, "nbasis must be in [1, 8]");
+  T2SH_REQ(d->nechoes >= d->nbasis && d->nechoes <= 4096, "nechoes must be in [nbasis, 4096]");
+  T2SH_REQ(d->nslices >= 1 && d->nslices <= 65535, "nslices must be in [1, 65535]");
+  T2SH_REQ(d->block >= 1 && d->block <= kMaxBlock, "block must be in [1, 16]");
+  T2SH_REQ(d->iters >= 0, "iters must be >= 0");
+  T2SH_REQ(std::isfinite(d->lambda) && d->lambda >= 0.f, "lambda must be finite and >= 0");
+  T2SH_REQ(std::isfinite(d->step), "step must be finite");
+  if (d->precision != T2SH_FP32) {
+    set_err("precision %d not implemented", d->precision);
+    return T2SH_EUNSUPPORTED;
+  }
+  T2SH_REQ((d->flags & ~(T2SH_NO_SHIFT | T2SH_HOST_IO)) == 0, "unknown flag bits");
+  Geom g{};
+  g.M = d->nmaps; g.K = d->nbasis; g.nz = d->nz;
+  if (llr_smem_bytes(g, d->block) > 200 * 1024) {
+    set_err("LLR band of %d x %d x %d x %d does not fit shared memory", d->nmaps, d->nbasis, d->block, d->nz);
+    return T2SH_EUNSUPPORTED;
+  }
+  return T2SH_OK;
+}
+
+}  // namespace
+
+struct t2sh_plan_s {
+  t2sh_dims d{};
+  cudaStream_t st = nullptr;
+  bool host_io = false;
+  Geom g{};
+  FftPlan py{}, pz{};
+  float2* tw_y = nullptr;
+  float2* tw_z = nullptr;
+  float* phi = nullptr;
+  uint8_t* mask = nullptr;
+  float* psi = nullptr;
+  float2* maps = nullptr;
+  float2* x = nullptr;
+  float2* z = nullptr;
+  float2* aty = nullptr;
+  float2* grad = nullptr;
+  float2* t = nullptr;
+  double* res = nullptr;
+  unsigned* red = nullptr;
+  void* stage = nullptr;  // host-IO staging of k-space input
+  size_t stage_bytes = 0;
+  std::vector<int32_t> shifts;
+  float mu = 1.f;
+  std::vector<void*> allocs;
+  // kernel timing (t2sh_timing_*)
+  static constexpr int kClasses = 6;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  size_t ev_next = 0;
+  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0};
+
+  template <typename T>
+  t2sh_status alloc(T** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_err("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+      return T2SH_ENOMEM;
+    }
+    allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return T2SH_OK;
+  }
+  ~t2sh_plan_s() {
+    for (void* p : allocs) cudaFree(p);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+  cudaEvent_t next_event() {
+    if (ev_next == ev_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_next++];
+  }
+};
+
+namespace {
+// Brackets one kernel launch with events when the plan records timings.
+struct KTimer {
+  t2sh_plan_s* p;
+  int cls;
+  cudaEvent_t a = nullptr;
+  KTimer(t2sh_plan_s* p_, int c) : p(p_), cls(c) {
+    p->launches[cls]++;
+    if (p->timing) {
+      a = p->next_event();
+      if (a) cudaEventRecord(a, p->st);
+    }
+  }
+  ~KTimer() {
+    if (p->timing && a) {
+      cudaEvent_t b = p->next_event();
+      if (b) {
+        cudaEventRecord(b, p->st);
+        p->ev_used.push_back({cls, {a, b}});
+      }
+    }
+  }
+};
+enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5 };
+}  // namespace
+
+namespace {
+
+t2sh_status normal_op(t2sh_plan_t p, const float2* x, float2* y) {
+  { KTimer k(p, KC_ROW_FWD); T2SH_CK(launch_row(p->g, ROW_FWD, p->pz, p->tw_z, p->maps, x, p->t, nullptr, p->st)); }
+  { KTimer k(p, KC_COL); T2SH_CK(launch_col(p->g, COL_NORMAL, p->py, p->tw_y, p->psi, p->phi, p->mask, p->t, p->t, p->st)); }
+  { KTimer k(p, KC_ROW_ADJ); T2SH_CK(launch_row(p->g, ROW_ADJ, p->pz, p->tw_z, p->maps, nullptr, p->t, y, p->st)); }
+  return T2SH_OK;
+}
+
+// A^H y for device k-space in either form, result in x.
+t2sh_status adjoint_data(t2sh_plan_t p, const void* y, int32_t kform, float2* x) {
+  const float2* proj = static_cast<const float2*>(y);
+  if (kform == T2SH_KSPACE_TE) {
+    KTimer k(p, KC_PROJ);
+    T2SH_CK(launch_project(p->g, p->phi, p->mask, static_cast<const float2*>(y), p->t, p->st));
+    proj = p->t;
+  }
+  { KTimer k(p, KC_COL); T2SH_CK(launch_col(p->g, COL_ADJ_DATA, p->py, p->tw_y, p->psi, p->phi, p->mask, proj, p->t, p->st)); }
+  { KTimer k(p, KC_ROW_ADJ); T2SH_CK(launch_row(p->g, ROW_ADJ, p->pz, p->tw_z, p->maps, nullptr, p->t, x, p->st)); }
+  return T2SH_OK;
+}
+
+size_t kspace_bytes(const t2sh_dims& d, int32_t kform) {
+  const long long N = (long long)d.ny * d.nz;
+  return cbytes((long long)d.nslices * d.ncoils * (kform == T2SH_KSPACE_TE ? d.nechoes : d.nbasis) * N);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t t2sh_version(void) { return 100; }
+
+const char* t2sh_last_error(void) { return g_err.c_str(); }
+
+t2sh_status t2sh_shifts(uint64_t seed, int32_t iters, int32_t block, int32_t* out) {
+  T2SH_REQ(out != nullptr || iters == 0, "out is NULL");
+  T2SH_REQ(iters >= 0 && block >= 1, "iters >= 0 and block >= 1 required");
+  for (int32_t i = 0; i < iters; ++i) {
+    const uint64_t h = splitmix64_at(seed, (uint64_t)i);
+    out[2 * i] = (int32_t)((h & 0xFFFFFFFFull) % (uint64_t)block);
+    out[2 * i + 1] = (int32_t)((h >> 32) % (uint64_t)block);
+  }
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_workspace_bytes(const t2sh_dims* dims, size_t* bytes) {
+  t2sh_status s = validate(dims);
+  if (s != T2SH_OK) return s;
+  T2SH_REQ(bytes != nullptr, "bytes is NULL");
+  *bytes = footprint(*dims).total();
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* mask, const void* maps, void* stream,
+                      t2sh_plan_t* out) {
+  if (out) *out = nullptr;
+  t2sh_status s = validate(dims);
+  if (s != T2SH_OK) return s;
+  T2SH_REQ(out && phi && mask && maps, "NULL argument");
+  t2sh_plan_s* p = new (std::nothrow) t2sh_plan_s();
+  if (!p) {
+    set_err("host allocation failed");
+    return T2SH_ENOMEM;
+  }
+  p->d = *dims;
+  p->st = static_cast<cudaStream_t>(stream);
+  p->host_io = (dims->flags & T2SH_HOST_IO) != 0;
+  const t2sh_dims& d = p->d;
+  Geom& g = p->g;
+  g.S = d.nslices; g.C = d.ncoils; g.M = d.nmaps; g.K = d.nbasis; g.T = d.nechoes;
+  g.ny = d.ny; g.nz = d.nz; g.P = d.nbasis * (d.nbasis + 1) / 2;
+  g.gsign = (((d.ny / 2) + (d.nz / 2)) & 1) ? -1.f : 1.f;
+  g.inv_sqrt_n = (float)(1.0 / std::sqrt((double)d.ny * d.nz));
+  if (!make_fft_plan(d.ny, p->py) || !make_fft_plan(d.nz, p->pz)) {
+    delete p;
+    set_err("no radix plan for ny=%d nz=%d", d.ny, d.nz);
+    return T2SH_EINVAL;
+  }
+  const Footprint f = footprint(d);
+#define ALLOC(ptr, bytes)                   \
+  do {                                      \
+    t2sh_status a_ = p->alloc(&(ptr), (bytes)); \
+    if (a_ != T2SH_OK) {                    \
+      delete p;                             \
+      return a_;                            \
+    }                                       \
+  } while (0)
+  ALLOC(p->maps, f.maps);
+  ALLOC(p->psi, f.psi);
+  ALLOC(p->phi, f.phi);
+  ALLOC(p->mask, f.mask);
+  ALLOC(p->x, f.vec);
+  ALLOC(p->z, f.vec);
+  ALLOC(p->aty, f.vec);
+  ALLOC(p->grad, f.vec);
+  ALLOC(p->t, f.t);
+  ALLOC(p->tw_y, cbytes(d.ny));
+  ALLOC(p->tw_z, cbytes(d.nz));
+  ALLOC(p->res, sizeof(double) * 2 * (size_t)(d.iters > 0 ? d.iters : 1));
+  ALLOC(p->red, 64);
+#undef ALLOC
+  // twiddles exp(-2 pi i m / n), computed in double
+  std::vector<float2> tw(std::max(d.ny, d.nz));
+  auto fill_tw = [&](int n) {
+    for (int m = 0; m < n; ++m) {
+      const double a = -2.0 * M_PI * (double)m / (double)n;
+      tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  };
+#define FAIL_CK(call)                                                                                 \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      set_err("%s failed: %s", #call, cudaGetErrorString(e_));                                      \
+      delete p;                                                                                     \
+      return T2SH_ECUDA;                                                                            \
+    }                                                                                               \
+  } while (0)
+  fill_tw(d.ny);
+  FAIL_CK(cudaMemcpyAsync(p->tw_y, tw.data(), cbytes(d.ny), cudaMemcpyHostToDevice, p->st));
+  FAIL_CK(cudaStreamSynchronize(p->st));
+  fill_tw(d.nz);
+  FAIL_CK(cudaMemcpyAsync(p->tw_z, tw.data(), cbytes(d.nz), cudaMemcpyHostToDevice, p->st));
+  const cudaMemcpyKind kind = p->host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  FAIL_CK(cudaMemcpyAsync(p->phi, phi, f.phi, kind, p->st));
+  FAIL_CK(cudaMemcpyAsync(p->mask, mask, f.mask, kind, p->st));
+  const float2* maps_src = static_cast<const float2*>(maps);
+  if (p->host_io) {
+    FAIL_CK(cudaMemcpyAsync(p->maps, maps, f.maps, kind, p->st));
+    maps_src = p->maps;
+  }
+  FAIL_CK(cudaMemsetAsync(p->red, 0, 64, p->st));
+  FAIL_CK(launch_maps_prep(g, maps_src, p->maps, p->red, p->st));
+  FAIL_CK(launch_psi_build(g, p->phi, p->mask, p->psi, p->red + 1, p->st));
+  unsigned bits[2];
+  FAIL_CK(cudaMemcpyAsync(bits, p->red, sizeof(bits), cudaMemcpyDeviceToHost, p->st));
+  FAIL_CK(cudaStreamSynchronize(p->st));
+#undef FAIL_CK
+  float lam_s, lam_psi;
+  std::memcpy(&lam_s, &bits[0], 4);
+  std::memcpy(&lam_psi, &bits[1], 4);
+  const double L = (double)lam_s * (double)lam_psi;
+  p->mu = d.step > 0.f ? d.step : (L > 0.0 ? (float)(1.0 / L) : 1.f);
+  p->shifts.assign(2 * (size_t)d.iters, 0);
+  if (!(d.flags & T2SH_NO_SHIFT)) t2sh_shifts(d.seed, d.iters, d.block, p->shifts.data());
+  *out = p;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_destroy(t2sh_plan_t p) {
+  if (!p) return T2SH_OK;
+  cudaStreamSynchronize(p->st);
+  if (p->stage) cudaFree(p->stage);
+  delete p;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_timing_enable(t2sh_plan_t p, int32_t enable) {
+  T2SH_REQ(p, "NULL plan");
+  if (enable) {
+    T2SH_CK(cudaStreamSynchronize(p->st));
+    p->ev_used.clear();
+    p->ev_next = 0;
+    for (int i = 0; i < t2sh_plan_s::kClasses; ++i) p->launches[i] = 0;
+  }
+  p->timing = enable != 0;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_timing_read(t2sh_plan_t p, int32_t cls, int64_t* launches, double* ms) {
+  T2SH_REQ(p && launches && ms, "NULL argument");
+  T2SH_REQ(cls >= 0 && cls < t2sh_plan_s::kClasses, "bad kernel class %d", cls);
+  T2SH_CK(cudaStreamSynchronize(p->st));
+  double tot = 0.0;
+  for (auto& u : p->ev_used) {
+    if (u.first != cls) continue;
+    float m = 0.f;
+    T2SH_CK(cudaEventElapsedTime(&m, u.second.first, u.second.second));
+    tot += m;
+  }
+  *launches = p->launches[cls];
+  *ms = tot;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_get_step(t2sh_plan_t p, float* step) {
+  T2SH_REQ(p && step, "NULL argument");
+  *step = p->mu;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_forward(t2sh_plan_t p, const void* x, void* y, int32_t kform) {
+  T2SH_REQ(p && x && y, "NULL argument");
+  T2SH_REQ(kform == T2SH_KSPACE_TE || kform == T2SH_KSPACE_PROJ, "bad kform %d", kform);
+  { KTimer k(p, KC_ROW_FWD); T2SH_CK(launch_row(p->g, ROW_FWD, p->pz, p->tw_z, p->maps, static_cast<const float2*>(x), p->t, nullptr, p->st)); }
+  { KTimer k(p, KC_COL); T2SH_CK(launch_col(p->g, kform == T2SH_KSPACE_TE ? COL_FWD_TE : COL_FWD_PROJ, p->py, p->tw_y, p->psi, p->phi,
+                     p->mask, p->t, static_cast<float2*>(y), p->st)); }
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_adjoint(t2sh_plan_t p, const void* y, int32_t kform, void* x) {
+  T2SH_REQ(p && x && y, "NULL argument");
+  T2SH_REQ(kform == T2SH_KSPACE_TE || kform == T2SH_KSPACE_PROJ, "bad kform %d", kform);
+  return adjoint_data(p, y, kform, static_cast<float2*>(x));
+}
+
+t2sh_status t2sh_normal_op(t2sh_plan_t p, const void* x, void* y) {
+  T2SH_REQ(p && x && y, "NULL argument");
+  return normal_op(p, static_cast<const float2*>(x), static_cast<float2*>(y));
+}
+
+t2sh_status t2sh_llr_prox(t2sh_plan_t p, void* x, float tau, int32_t sy, int32_t sz) {
+  T2SH_REQ(p && x, "NULL argument");
+  T2SH_REQ(std::isfinite(tau) && tau >= 0.f, "tau must be finite and >= 0");
+  T2SH_REQ(sy >= 0 && sz >= 0 && sy < p->d.block && sz < p->d.block, "shift must be in [0, block)");
+  FistaArgs a{};
+  a.mu = 0.f; a.tau = tau; a.beta = 0.f; a.sy = sy; a.sz = sz; a.b = p->d.block; a.res = nullptr;
+  KTimer k(p, KC_LLR);
+  T2SH_CK(launch_llr(p->g, a, static_cast<float2*>(x), nullptr, nullptr, nullptr, p->st));
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* alpha_out, double* residual_out) {
+  T2SH_REQ(p && kspace && alpha_out, "NULL argument");
+  T2SH_REQ(kform == T2SH_KSPACE_TE || kform == T2SH_KSPACE_PROJ, "bad kform %d", kform);
+  const t2sh_dims& d = p->d;
+  const size_t vec = footprint(d).vec;
+  const void* ky = kspace;
+  if (p->host_io) {
+    const size_t kb = kspace_bytes(d, kform);
+    if (p->stage_bytes < kb) {
+      if (p->stage) cudaFree(p->stage);
+      p->stage = nullptr;
+      p->stage_bytes = 0;
+      if (cudaMalloc(&p->stage, kb) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("cudaMalloc(%zu) for the k-space stage failed", kb);
+        return T2SH_ENOMEM;
+      }
+      p->stage_bytes = kb;
+    }
+    T2SH_CK(cudaMemcpyAsync(p->stage, kspace, kb, cudaMemcpyHostToDevice, p->st));
+    ky = p->stage;
+  }
+  t2sh_status s = adjoint_data(p, ky, kform, p->aty);
+  if (s != T2SH_OK) return s;
+  T2SH_CK(cudaMemsetAsync(p->x, 0, vec, p->st));
+  T2SH_CK(cudaMemsetAsync(p->z, 0, vec, p->st));
+  if (residual_out) T2SH_CK(cudaMemsetAsync(p->res, 0, sizeof(double) * 2 * (size_t)d.iters, p->st));
+  double tk = 1.0;
+  for (int it = 0; it < d.iters; ++it) {
+    if (it == 0) {
+      T2SH_CK(cudaMemsetAsync(p->grad, 0, vec, p->st));  // z_0 = 0
+    } else {
+      s = normal_op(p, p->z, p->grad);
+      if (s != T2SH_OK) return s;
+    }
+    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * tk * tk));
+    FistaArgs a{};
+    a.mu = p->mu;
+    a.tau = p->mu * d.lambda;
+    a.beta = (float)((tk - 1.0) / tn);
+    a.sy = p->shifts[2 * it];
+    a.sz = p->shifts[2 * it + 1];
+    a.b = d.block;
+    a.res = residual_out ? p->res + 2 * it : nullptr;
+    { KTimer k(p, KC_LLR); T2SH_CK(launch_llr(p->g, a, p->x, p->z, p->grad, p->aty, p->st)); }
+    tk = tn;
+  }
+  T2SH_CK(cudaMemcpyAsync(alpha_out, p->x, vec, p->host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          p->st));
+  if (residual_out && d.iters > 0) {
+    std::vector<double> r(2 * (size_t)d.iters);
+    T2SH_CK(cudaMemcpyAsync(r.data(), p->res, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, p->st));
+    T2SH_CK(cudaStreamSynchronize(p->st));
+    for (int it = 0; it < d.iters; ++it)
+      residual_out[it] = r[2 * it + 1] > 0.0 ? std::sqrt(r[2 * it] / r[2 * it + 1]) : 0.0;
+  } else if (p->host_io) {
+    T2SH_CK(cudaStreamSynchronize(p->st));
+  }
+  return T2SH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+// Device building blocks of the T2 Shuffling solver: complex arithmetic, the
+// register radix butterflies and an in-place shared-memory Stockham FFT over a batch
+// of lines, and a Jacobi eigensolver for the small Hermitian Gram matrices of the LLR
+// prox.  Included by the kernel translation units only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "t2sh_plan.h"
+
+namespace t2sh {
+
+// ---------------------------------------------------------------------------------
+// complex float helpers (interleaved float2)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+// a += b * c
+__device__ __forceinline__ void cfma(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+  a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+// a += conj(b) * c
+__device__ __forceinline__ void cfmac(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
+  a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot_i(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 twiddle_mul(float2 a, float2 w) {  // w = exp(-2 pi i m / N)
+  return INV ? cmulc(w, a) : cmul(a, w);
+}
+
+// ---------------------------------------------------------------------------------
+// Radix-R DFTs in registers, X_k = sum_n x_n exp(-+2 pi i n k / R) (sign + for INV).
+// Constants are exact trigonometric values written out.
+// ---------------------------------------------------------------------------------
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+  const float c = -0.5f, s = 0.86602540378443865f;  // cos(2pi/3), sin(2pi/3)
+  float2 t1 = cadd(v[1], v[2]);
+  float2 t2 = make_float2(fmaf(c, t1.x, v[0].x), fmaf(c, t1.y, v[0].y));
+  float2 t3 = cscale(csub(v[1], v[2]), s);  // s (x1 - x2)
+  v[0] = cadd(v[0], t1);
+  float2 r = rot_i<INV>(t3);  // -+ i s (x1 - x2)
+  v[1] = cadd(t2, r);
+  v[2] = csub(t2, r);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* v) {
+  float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  float2 c = cadd(v[1], v[3]), d = rot_i<INV>(csub(v[1], v[3]));
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  v[1] = cadd(b, d);
+  v[3] = csub(b, d);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft5(float2* v) {
+  const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;  // cos(2pi/5), cos(4pi/5)
+  const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;   // sin(2pi/5), sin(4pi/5)
+  float2 u1 = cadd(v[1], v[4]), u2 = cadd(v[2], v[3]);
+  float2 w1 = csub(v[1], v[4]), w2 = csub(v[2], v[3]);
+  float2 x0 = v[0];
+  float2 a1 = make_float2(x0.x + c1 * u1.x + c2 * u2.x, x0.y + c1 * u1.y + c2 * u2.y);
+  float2 a2 = make_float2(x0.x + c2 * u1.x + c1 * u2.x, x0.y + c2 * u1.y + c1 * u2.y);
+  float2 b1 = make_float2(s1 * w1.x + s2 * w2.x, s1 * w1.y + s2 * w2.y);
+  float2 b2 = make_float2(s2 * w1.x - s1 * w2.x, s2 * w1.y - s1 * w2.y);
+  float2 r1 = rot_i<INV>(b1), r2 = rot_i<INV>(b2);
+  v[0] = cadd(x0, cadd(u1, u2));
+  v[1] = cadd(a1, r1);
+  v[4] = csub(a1, r1);
+  v[2] = cadd(a2, r2);
+  v[3] = csub(a2, r2);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  const float h = 0.70710678118654752f;
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  // w8^k, k = 0..3: 1, (1 -+ i)/sqrt2, -+i, (-1 -+ i)/sqrt2
+  float2 o1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                  : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+  float2 o2 = rot_i<INV>(o[2]);
+  float2 o3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                  : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  // w16^k = cos(pi k / 8) -+ i sin(pi k / 8)
+  const float C[8] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                      0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f};
+  const float S[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                      1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+  float2 e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft8<INV>(e);
+  dft8<INV>(o);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float2 w = make_float2(C[k], INV ? S[k] : -S[k]);
+    float2 t = cmul(o[k], w);
+    v[k] = cadd(e[k], t);
+    v[k + 8] = csub(e[k], t);
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<INV>(v);
+  else if constexpr (R == 4) dft4<INV>(v);
+  else if constexpr (R == 5) dft5<INV>(v);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+}
+
+// ---------------------------------------------------------------------------------
+// In-place Stockham autosort FFT of `nbatch` lines of length p.n held in shared
+// memory (line b at buf[b * ld], unit stride), natural order in and out, unnormalised.
+// Each pass first pulls every butterfly's inputs into registers, synchronises, then
+// writes its outputs, so one buffer suffices.  Consecutive threads take consecutive
+// lines of the same butterfly: with ld odd the accesses are bank-conflict free and
+// the twiddle read is a broadcast.  Requires nbatch * p.n <= kStage * blockDim.x.
+//   tw[m] = exp(-2 pi i m / n), m < n (shared memory copy).
+// ---------------------------------------------------------------------------------
+constexpr int kStageRegs = 20;  // >= ceil(kStage / R) * R for every radix used
+constexpr int kStageBf = 8;     // >= ceil(kStage / R) for every radix used
+
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_pass(float2* buf, int ld, int nbatch, int n, int ns, const float2* tw,
+                                              float2 (&v)[kStageRegs], int (&dst)[kStageBf]) {
+  constexpr int UMAX = (kStage + R - 1) / R;
+  static_assert(UMAX * R <= kStageRegs && UMAX <= kStageBf, "staging registers");
+  const int nbf = n / R;
+  const int total = nbf * nbatch;
+  const int tstride = n / (ns * R);
+  const int nthr = blockDim.x;
+#pragma unroll
+  for (int u = 0; u < UMAX; ++u) {
+    const int idx = threadIdx.x + u * nthr;
+    dst[u] = -1;
+    if (idx < total) {
+      const int j = idx / nbatch;
+      const int b = idx - j * nbatch;
+      const float2* src = buf + b * ld + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u * R + r] = src[r * nbf];
+      const int jm = j % ns;
+      if (ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[u * R + r] = twiddle_mul<INV>(v[u * R + r], tw[r * jm * tstride]);
+      }
+      dft_r<R, INV>(v + u * R);
+      dst[u] = b * ld + (j - jm) * R + jm;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < UMAX; ++u) {
+    if (dst[u] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[dst[u] + r * ns] = v[u * R + r];
+    }
+  }
+  __syncthreads();
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft_lines(float2* buf, int ld, int nbatch, const FftPlan& p, const float2* tw) {
+  float2 v[kStageRegs];
+  int dst[kStageBf];
+  for (int q = 0; q < p.npass; ++q) {
+    const int ns = p.ns[q];
+    switch (p.radix[q]) {
+      case 16: stockham_pass<16, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 8: stockham_pass<8, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 4: stockham_pass<4, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 2: stockham_pass<2, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 3: stockham_pass<3, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 5: stockham_pass<5, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      default: break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Cyclic Jacobi eigensolver for a Hermitian K x K matrix, real type T.  On entry
+// (ar, ai) hold the full matrix; on exit the diagonal of ar holds the eigenvalues and
+// (vr, vi) the eigenvectors as columns.  Each rotation first makes a_pq real with a
+// diagonal phase, then applies the real Jacobi rotation with tan(theta) the smaller
+// root of t^2 + 2 t theta - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq).  Sweeps stop
+// when the off-diagonal mass is below (eps^2) of the diagonal mass.
+// ---------------------------------------------------------------------------------
+template <typename T> struct JacobiTol;
+template <> struct JacobiTol<double> { static constexpr double rel2 = 1e-30; };
+template <> struct JacobiTol<float> { static constexpr float rel2 = 1e-13f; };
+
+template <typename T, int K>
+__device__ __forceinline__ void herm_jacobi(T (&ar)[K][K], T (&ai)[K][K], T (&vr)[K][K], T (&vi)[K][K],
+                                            int max_sweeps) {
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      vr[i][j] = (i == j) ? T(1) : T(0);
+      vi[i][j] = T(0);
+    }
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = 0, diag = 0;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      diag += ar[p][p] * ar[p][p];
+#pragma unroll
+      for (int q = p + 1; q < K; ++q) off += ar[p][q] * ar[p][q] + ai[p][q] * ai[p][q];
+    }
+    if (!(off > JacobiTol<T>::rel2 * diag)) break;
+#pragma unroll
+    for (int p = 0; p < K - 1; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < K; ++q) {
+        const T xr = ar[p][q], xi = ai[p][q];
+        const T r2 = xr * xr + xi * xi;
+        if (r2 > T(0)) {
+          const T r = sqrt(r2);
+          // phase: column q *= d, row q *= conj(d), d = conj(a_pq) / |a_pq|
+          const T dr = xr / r, di = -xi / r;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            if (k != q) {
+              const T yr = ar[k][q] * dr - ai[k][q] * di;
+              const T yi = ar[k][q] * di + ai[k][q] * dr;
+              ar[k][q] = yr; ai[k][q] = yi;
+              ar[q][k] = yr; ai[q][k] = -yi;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const T yr = vr[k][q] * dr - vi[k][q] * di;
+            const T yi = vr[k][q] * di + vi[k][q] * dr;
+            vr[k][q] = yr; vi[k][q] = yi;
+          }
+          // a_pq is now the real r: real rotation on rows/columns p, q
+          const T theta = (ar[q][q] - ar[p][p]) / (T(2) * r);
+          T t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
+          if (theta < T(0)) t = -t;
+          const T c = T(1) / sqrt(t * t + T(1));
+          const T s = t * c;
+          ar[p][p] -= t * r;
+          ar[q][q] += t * r;
+          ar[p][q] = T(0); ar[q][p] = T(0);
+          ai[p][q] = T(0); ai[q][p] = T(0);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            if (k != p && k != q) {
+              const T akp_r = ar[k][p], akp_i = ai[k][p];
+              const T akq_r = ar[k][q], akq_i = ai[k][q];
+              const T nkp_r = c * akp_r - s * akq_r, nkp_i = c * akp_i - s * akq_i;
+              const T nkq_r = s * akp_r + c * akq_r, nkq_i = s * akp_i + c * akq_i;
+              ar[k][p] = nkp_r; ai[k][p] = nkp_i; ar[p][k] = nkp_r; ai[p][k] = -nkp_i;
+              ar[k][q] = nkq_r; ai[k][q] = nkq_i; ar[q][k] = nkq_r; ai[q][k] = -nkq_i;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const T vkp_r = vr[k][p], vkp_i = vi[k][p];
+            const T vkq_r = vr[k][q], vkq_i = vi[k][q];
+            vr[k][p] = c * vkp_r - s * vkq_r; vi[k][p] = c * vkp_i - s * vkq_i;
+            vr[k][q] = s * vkp_r + c * vkq_r; vi[k][q] = s * vkp_i + c * vkq_i;
+          }
+        }
+      }
+    }
+  }
+}
+
+// sign (-1)^(a) as float
+__device__ __forceinline__ float parity_sign(int a) { return (a & 1) ? -1.0f : 1.0f; }
+
+}  // namespace t2sh

@@ -1,0 +1,78 @@
+// Internal structures shared by the host runtime (t2sh_api.cu) and the kernel
+// translation units.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace t2sh {
+
+constexpr int kThreads = 256;                    // threads of the prep and LLR CTAs
+constexpr int kFftThreads = 512;                 // threads of the row / column FFT CTAs
+constexpr int kStage = 16;                       // complex values a thread stages per FFT pass
+constexpr int kMaxLineElems = kStage * kFftThreads;  // complex elements one CTA transforms at once
+constexpr int kMaxPass = 8;
+constexpr int kMaxK = 8;
+constexpr int kMaxM = 2;
+constexpr int kMaxBlock = 16;
+
+// Radix plan of a length-n FFT: pass q has radix radix[q] and ns[q] = prod of the
+// radices of passes 0..q-1 (Stockham autosort).
+struct FftPlan {
+  int n;
+  int npass;
+  int radix[kMaxPass];
+  int ns[kMaxPass];
+};
+
+// Geometry of one batch of slices, passed by value to every kernel.
+struct Geom {
+  int S, C, M, K, T;   // slices, coils, map sets, basis size, echoes
+  int ny, nz;          // slice matrix
+  int P;               // K (K + 1) / 2: stored entries of Psi(n)
+  float gsign;         // (-1)^(ny/2 + nz/2): global sign of the centred DFT
+  float inv_sqrt_n;    // 1 / sqrt(ny nz)
+};
+
+// Column-pass (ky direction) modes.
+enum ColMode : int {
+  COL_NORMAL = 0,    // DFT_y, Psi (pre-scaled by 1/N), IDFT_y                 (normal operator)
+  COL_ADJ_DATA = 1,  // multiply by gsign (-1)^(ky+kz) / sqrt(N), IDFT_y          (A^H y)
+  COL_FWD_PROJ = 2,  // DFT_y, multiply by gsign (-1)^(ky+kz) / sqrt(N), Psi * N  (Phi^T P A x)
+  COL_FWD_TE = 3     // DFT_y, multiply by gsign (-1)^(ky+kz) / sqrt(N), P_t Phi  (A x, per echo)
+};
+
+// Row-pass (kz direction) modes.
+enum RowMode : int {
+  ROW_FWD = 0,  // t[c][k] = DFT_z( sum_m S'_{c,m} x_{m,k} )
+  ROW_ADJ = 1   // out[m][k] = sum_c conj(S'_{c,m}) IDFT_z( t[c][k] )
+};
+
+struct FistaArgs {
+  float mu;      // step
+  float tau;     // mu * lambda
+  float beta;    // (t_k - 1) / t_{k+1}
+  int sy, sz;    // LLR shift of this iteration
+  int b;         // block edge
+  double* res;   // nullable: accumulates {sum |x_{k+1} - x_k|^2, sum |x_{k+1}|^2}
+};
+
+// ------------------------------ launchers -----------------------------------------
+// All return the cudaGetLastError() of their launch.
+cudaError_t launch_maps_prep(const Geom& g, const float2* maps_in, float2* maps_out, unsigned* lam_s_bits,
+                             cudaStream_t st);
+cudaError_t launch_psi_build(const Geom& g, const float* phi, const uint8_t* mask, float* psi,
+                             unsigned* lam_psi_bits, cudaStream_t st);
+cudaError_t launch_project(const Geom& g, const float* phi, const uint8_t* mask, const float2* y_te,
+                           float2* y_proj, cudaStream_t st);
+cudaError_t launch_row(const Geom& g, RowMode mode, const FftPlan& pz, const float2* tw_z, const float2* maps,
+                       const float2* x, float2* t, float2* out, cudaStream_t st);
+cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const float2* tw_y, const float* psi,
+                       const float* phi, const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st);
+cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
+                       const float2* aty, cudaStream_t st);
+
+int row_rows_per_cta(const Geom& g);
+int col_cols_per_cta(const Geom& g);
+
+}  // namespace t2sh

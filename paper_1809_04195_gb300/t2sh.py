@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libt2sh.so (C ABI in include/t2sh.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.
+Device arrays are torch CUDA tensors (PyTorch supplies device memory and streams);
+with ``host_io=True`` the plan takes host arrays (numpy or CPU tensors) and the library
+does the copies.  There is no fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libt2sh.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "t2sh.h")
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, EBUSY = range(7)
+FP32, MIXED_BF16 = 0, 1
+KSPACE_TE, KSPACE_PROJ = 0, 1
+NO_SHIFT, HOST_IO = 0x1, 0x2
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "ETIMEOUT", 6: "EBUSY"}
+
+
+class T2shError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("ncoils", ctypes.c_int32),
+                ("nmaps", ctypes.c_int32), ("nechoes", ctypes.c_int32), ("nbasis", ctypes.c_int32),
+                ("nslices", ctypes.c_int32), ("block", ctypes.c_int32), ("lam", ctypes.c_float),
+                ("iters", ctypes.c_int32), ("seed", ctypes.c_uint64), ("step", ctypes.c_float),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+def make_dims(ny, nz, ncoils, nechoes, nbasis, nslices=1, nmaps=1, block=8, lam=0.0, iters=0, seed=0,
+              step=0.0, precision=FP32, flags=0) -> Dims:
+    return Dims(ny, nz, ncoils, nmaps, nechoes, nbasis, nslices, block, lam, iters, seed, step, precision, flags)
+
+
+_lib = None
+_vp, _i32, _u64, _f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_float
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1809_04195_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "t2sh_plan": [ctypes.POINTER(Dims), _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)],
+            "t2sh_destroy": [_vp],
+            "t2sh_forward": [_vp, _vp, _vp, _i32],
+            "t2sh_adjoint": [_vp, _vp, _i32, _vp],
+            "t2sh_normal_op": [_vp, _vp, _vp],
+            "t2sh_llr_prox": [_vp, _vp, _f32, _i32, _i32],
+            "t2sh_solve": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
+            "t2sh_get_step": [_vp, ctypes.POINTER(_f32)],
+            "t2sh_shifts": [_u64, _i32, _i32, ctypes.POINTER(_i32)],
+            "t2sh_workspace_bytes": [ctypes.POINTER(Dims), ctypes.POINTER(ctypes.c_size_t)],
+            "t2sh_timing_enable": [_vp, _i32],
+            "t2sh_timing_read": [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.t2sh_last_error.argtypes = []
+        L.t2sh_last_error.restype = ctypes.c_char_p
+        L.t2sh_version.argtypes = []
+        L.t2sh_version.restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/t2sh.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:t2sh_status|const char\*|int32_t)\s+(t2sh_\w+)\s*\(", txt, re.M)))
+
+
+def _check(status: int):
+    if status != OK:
+        raise T2shError(status, lib().t2sh_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().t2sh_last_error().decode()
+
+
+def version() -> int:
+    return int(lib().t2sh_version())
+
+
+def shifts(seed: int, iters: int, block: int) -> np.ndarray:
+    """LLR shift table [iters][2] (sy, sz), host-only."""
+    out = np.zeros((max(iters, 0), 2), np.int32)
+    _check(lib().t2sh_shifts(seed, iters, block, out.ctypes.data_as(ctypes.POINTER(_i32))))
+    return out
+
+
+def workspace_bytes(dims: Dims) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().t2sh_workspace_bytes(ctypes.byref(dims), ctypes.byref(n)))
+    return int(n.value)
+
+
+def _ptr(t, dtype, shape, host: bool):
+    """Data pointer of a contiguous array with the expected dtype and shape."""
+    import torch
+    if isinstance(t, np.ndarray):
+        if not host:
+            raise TypeError("numpy arrays are host memory: pass torch CUDA tensors or use host_io=True")
+        want = {torch.complex64: np.complex64, torch.float32: np.float32, torch.uint8: np.uint8}[dtype]
+        if t.dtype != want or not t.flags["C_CONTIGUOUS"] or tuple(t.shape) != tuple(shape):
+            raise ValueError(f"expected C-contiguous {want} {tuple(shape)}, got {t.dtype} {t.shape}")
+        return ctypes.c_void_p(t.ctypes.data)
+    if t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    if host == t.is_cuda:
+        raise ValueError("host_io plans take host arrays; other plans take CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """One batch of slices sharing a basis, a sampling pattern and dimensions.
+
+    phi [T][K] float32, mask [T][ny][nz] uint8, maps [S][C][M][ny][nz] complex64."""
+
+    def __init__(self, dims: Dims, phi, mask, maps, stream=None):
+        import torch
+        self.dims = dims
+        self.host_io = bool(dims.flags & HOST_IO)
+        d = dims
+        self.S, self.C, self.M, self.K, self.T = d.nslices, d.ncoils, d.nmaps, d.nbasis, d.nechoes
+        self.ny, self.nz = d.ny, d.nz
+        self.vec_shape = (self.S, self.M, self.K, self.ny, self.nz)
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        h = ctypes.c_void_p(0)
+        _check(lib().t2sh_plan(ctypes.byref(d),
+                               _ptr(phi, torch.float32, (self.T, self.K), self.host_io),
+                               _ptr(mask, torch.uint8, (self.T, self.ny, self.nz), self.host_io),
+                               _ptr(maps, torch.complex64, (self.S, self.C, self.M, self.ny, self.nz), self.host_io),
+                               sp, ctypes.byref(h)))
+        self._h = h
+
+    # -- helpers --------------------------------------------------------------------
+    def _kshape(self, kform):
+        return (self.S, self.C, self.T if kform == KSPACE_TE else self.K, self.ny, self.nz)
+
+    def _dev(self, t, shape):
+        import torch
+        return _ptr(t, torch.complex64, shape, False)
+
+    def _empty(self, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.complex64, device="cuda")
+
+    @property
+    def step(self) -> float:
+        v = ctypes.c_float(0)
+        _check(lib().t2sh_get_step(self._h, ctypes.byref(v)))
+        return float(v.value)
+
+    # -- operators ------------------------------------------------------------------
+    def forward(self, x, kform=KSPACE_PROJ, out=None):
+        out = self._empty(self._kshape(kform)) if out is None else out
+        _check(lib().t2sh_forward(self._h, self._dev(x, self.vec_shape), self._dev(out, self._kshape(kform)), kform))
+        return out
+
+    def adjoint(self, y, kform=KSPACE_PROJ, out=None):
+        out = self._empty(self.vec_shape) if out is None else out
+        _check(lib().t2sh_adjoint(self._h, self._dev(y, self._kshape(kform)), kform, self._dev(out, self.vec_shape)))
+        return out
+
+    def normal_op(self, x, out=None):
+        out = self._empty(self.vec_shape) if out is None else out
+        _check(lib().t2sh_normal_op(self._h, self._dev(x, self.vec_shape), self._dev(out, self.vec_shape)))
+        return out
+
+    def llr_prox(self, x, tau: float, sy: int, sz: int):
+        """In place."""
+        _check(lib().t2sh_llr_prox(self._h, self._dev(x, self.vec_shape), float(tau), int(sy), int(sz)))
+        return x
+
+    def solve(self, kspace, kform=KSPACE_PROJ, out=None, residual: bool = False):
+        """FISTA solve; returns alpha (and the per-iteration relative change if asked)."""
+        import torch
+        if self.host_io:
+            if out is None:
+                out = np.empty(self.vec_shape, np.complex64)
+            kp = _ptr(kspace, torch.complex64, self._kshape(kform), True)
+            op = _ptr(out, torch.complex64, self.vec_shape, True)
+        else:
+            out = self._empty(self.vec_shape) if out is None else out
+            kp, op = self._dev(kspace, self._kshape(kform)), self._dev(out, self.vec_shape)
+        res = None
+        rp = None
+        if residual:
+            res = np.zeros(max(self.dims.iters, 0), np.float64)
+            rp = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().t2sh_solve(self._h, kp, kform, op, rp))
+        return (out, res) if residual else out
+
+    # -- kernel timing ----------------------------------------------------------------
+    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project"}
+
+    def timing(self, enable: bool):
+        _check(lib().t2sh_timing_enable(self._h, 1 if enable else 0))
+
+    def timing_read(self) -> dict:
+        """{class name: (launches, total ms)} since timing(True)."""
+        out = {}
+        for c, name in self.KERNEL_CLASSES.items():
+            n = ctypes.c_int64(0)
+            ms = ctypes.c_double(0)
+            _check(lib().t2sh_timing_read(self._h, c, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (int(n.value), float(ms.value))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().t2sh_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/t2sh.h declares, and its host-only entry points behave (no GPU calls)."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1809_04195_gb300 import build as B
+from paper_1809_04195_gb300 import t2sh
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return t2sh.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = t2sh.header_symbols()
+    assert len(declared) >= 12
+    nm = subprocess.run(["nm", "-D", "--defined-only", t2sh.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in nm.splitlines() if ln.strip()}
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    for s in declared:
+        assert getattr(lib, s) is not None
+
+
+def test_version(lib):
+    assert t2sh.version() == 100
+
+
+@pytest.mark.parametrize("seed,b", [(1809, 8), (1810, 8), (0, 12), (2**63 + 12345, 5), (7, 1)])
+def test_shift_table_bit_exact_with_oracle(lib, seed, b):
+    got = t2sh.shifts(seed, 300, b)
+    ref = O.llr_shifts(seed, 300, b)
+    assert np.array_equal(got.astype(np.int64), ref)
+
+
+def test_workspace_bytes_formula(lib):
+    d = t2sh.make_dims(256, 160, 12, 80, 4, nslices=320, block=8, iters=100)
+    N = 256 * 160
+    vec = 320 * 1 * 4 * N * 8
+    expect = (320 * 12 * 1 * N * 8 + 10 * N * 4 + 80 * 4 * 4 + 80 * N + 4 * vec + 320 * 12 * 4 * N * 8
+              + (256 + 160) * 8 + 8 * 2 * 100 + 64)
+    assert t2sh.workspace_bytes(d) == expect
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(ny=63), t2sh.EINVAL),          # odd
+    (dict(nz=14 * 7), t2sh.EINVAL),      # 98 = 2 * 7^2 is not 2/3/5-smooth
+    (dict(ny=4), t2sh.EINVAL),           # too small
+    (dict(nbasis=9), t2sh.EINVAL),
+    (dict(nmaps=3), t2sh.EINVAL),
+    (dict(block=0), t2sh.EINVAL),
+    (dict(nechoes=3), t2sh.EINVAL),      # T < K
+    (dict(precision=t2sh.MIXED_BF16), t2sh.EUNSUPPORTED),
+    (dict(flags=0x80), t2sh.EINVAL),
+])
+def test_invalid_dims_rejected(lib, kw, status):
+    base = dict(ny=64, nz=48, ncoils=8, nechoes=32, nbasis=4, nslices=1, block=8, iters=10)
+    base.update(kw)
+    d = t2sh.make_dims(**base)
+    n = ctypes.c_size_t(0)
+    assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == status
+    assert len(t2sh.last_error()) > 0
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.t2sh_workspace_bytes(None, None) == t2sh.EINVAL
+    assert lib.t2sh_normal_op(None, None, None) == t2sh.EINVAL
+    assert lib.t2sh_destroy(None) == t2sh.OK

@@ -1,0 +1,251 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on seeded inputs.
+
+Tolerances (float32 arithmetic against float64):
+  * single operators (A, A^H, A^H A, LLR prox): NRMSE <= 1e-5.  A 2D FFT pair
+    accumulates about log2(ny nz) ~ 12-16 roundings of u = 6e-8 per stage, plus the
+    K-term Psi and C-term coil sums: expected ~1e-6, bound 1e-5.
+  * the FISTA solve: per-slice NRMSE <= 1e-4 (the stated requirement of the fp32 path).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import t2sh_synth as synth
+
+from t2sh_cases import crandn, proj_scan, te_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+SOLVE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_04195_gb300 import build as B
+    B.build()
+    from paper_1809_04195_gb300 import t2sh
+    return t2sh
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def c64(a):
+    return dev(np.asarray(a, np.complex64))
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def nrmse(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def make_plan(T, phi, mask, maps, **kw):
+    S, C, M, ny, nz = maps.shape
+    Tn, K = phi.shape
+    d = T.make_dims(ny, nz, C, Tn, K, nslices=S, nmaps=M, **kw)
+    return T.Plan(d, dev(phi.astype(np.float32)), dev(mask.astype(np.uint8)), c64(maps))
+
+
+def r32(phi=None, maps=None):
+    """The inputs as the float32 / complex64 values the GPU receives, widened back."""
+    out = []
+    if phi is not None:
+        out.append(phi.astype(np.float32).astype(np.float64))
+    if maps is not None:
+        out.append(maps.astype(np.complex64).astype(np.complex128))
+    return out
+
+
+def random_problem(seed, S, ny, nz, C, T_, K, M, frac=0.15):
+    rng = np.random.default_rng(seed)
+    phi = synth.t2_basis(T_, K)
+    mask = synth.vd_masks(T_, ny, nz, frac, rng)
+    maps = np.stack([synth.coil_maps(C, ny, nz, rng, M=M) for _ in range(S)])
+    phi, maps = r32(phi, maps)
+    return rng, phi, mask, maps
+
+
+SHAPES = [
+    # S, ny, nz, C, T, K, M
+    (1, 64, 48, 8, 32, 4, 1),
+    (3, 40, 24, 3, 12, 4, 2),
+    (2, 60, 36, 4, 10, 3, 1),   # radix-3/5 passes, K < 4
+    (2, 48, 30, 2, 14, 6, 1),   # K > 4 path
+    (1, 256, 160, 2, 16, 4, 1),  # the knee slice matrix
+]
+
+
+@pytest.mark.parametrize("S,ny,nz,C,Tn,K,M", SHAPES)
+def test_operators_match_oracle(T, S, ny, nz, C, Tn, K, M):
+    rng, phi, mask, maps = random_problem(100 + ny + K, S, ny, nz, C, Tn, K, M)
+    with make_plan(T, phi, mask, maps, block=8) as p:
+        x = crandn(rng, S, M, K, ny, nz)
+        y = crandn(rng, S, C, Tn, ny, nz)
+        ytil = crandn(rng, S, C, K, ny, nz)
+        g_fwd_te = host(p.forward(c64(x), T.KSPACE_TE))
+        g_fwd_pr = host(p.forward(c64(x), T.KSPACE_PROJ))
+        g_adj_te = host(p.adjoint(c64(y), T.KSPACE_TE))
+        g_adj_pr = host(p.adjoint(c64(ytil), T.KSPACE_PROJ))
+        g_nrm = host(p.normal_op(c64(x)))
+        torch.cuda.synchronize()
+    psi = O.space_time_kernel(mask, phi)
+    xs = x.astype(np.complex64).astype(np.complex128)
+    ys = y.astype(np.complex64).astype(np.complex128)
+    yts = ytil.astype(np.complex64).astype(np.complex128)
+    for s in range(S):
+        assert nrmse(g_fwd_te[s], O.forward(xs[s], maps[s], mask, phi)) < OP_TOL
+        assert nrmse(g_fwd_pr[s], O.project(O.forward(xs[s], maps[s], mask, phi), mask, phi)) < OP_TOL
+        assert nrmse(g_adj_te[s], O.adjoint(ys[s], maps[s], mask, phi)) < OP_TOL
+        assert nrmse(g_adj_pr[s], O.adjoint_projected(yts[s], maps[s])) < OP_TOL
+        assert nrmse(g_nrm[s], O.normal(xs[s], maps[s], psi)) < OP_TOL
+
+
+def test_adjoint_identity_on_gpu(T):
+    rng, phi, mask, maps = random_problem(7, 2, 64, 48, 4, 16, 4, 1)
+    with make_plan(T, phi, mask, maps) as p:
+        x = c64(crandn(rng, 2, 1, 4, 64, 48))
+        y = c64(crandn(rng, 2, 4, 16, 64, 48) * mask[None, None])
+        ax = p.forward(x, T.KSPACE_TE)
+        ahy = p.adjoint(y, T.KSPACE_TE)
+        lhs = torch.vdot(y.flatten().to(torch.complex128), ax.flatten().to(torch.complex128)).item()
+        rhs = torch.vdot(ahy.flatten().to(torch.complex128), x.flatten().to(torch.complex128)).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_step_matches_oracle(T):
+    _, phi, mask, maps = random_problem(9, 3, 64, 48, 6, 20, 4, 2)
+    with make_plan(T, phi, mask, maps) as p:
+        mu = p.step
+    L = max(O.lipschitz(maps[s], O.space_time_kernel(mask, phi)) for s in range(3))
+    assert abs(mu - 1.0 / L) <= 1e-5 / L
+
+
+@pytest.mark.parametrize("ny,nz,b,sy,sz,M,K", [
+    (64, 48, 8, 3, 5, 1, 4),
+    (60, 44, 8, 7, 2, 1, 4),    # partial blocks on both axes
+    (40, 24, 6, 5, 0, 2, 4),    # two map sets
+    (48, 30, 8, 1, 6, 1, 6),    # K > 4
+    (256, 160, 8, 0, 0, 1, 4),
+])
+def test_llr_prox_matches_oracle(T, ny, nz, b, sy, sz, M, K):
+    rng, phi, mask, maps = random_problem(ny * nz + b, 2, ny, nz, 2, max(K, 8), K, M)
+    x = crandn(rng, 2, M, K, ny, nz)
+    # blocks with a decaying spectrum so that some singular values fall under tau
+    x[..., ::2, :] *= 0.3
+    tau = 0.8
+    with make_plan(T, phi, mask, maps, block=b) as p:
+        xg = c64(x)
+        p.llr_prox(xg, tau, sy, sz)
+        got = host(xg)
+    xs = x.astype(np.complex64).astype(np.complex128)
+    for s in range(2):
+        ref = O.llr_prox(xs[s], b, tau, sy, sz)
+        assert nrmse(got[s], ref) < OP_TOL
+
+
+def test_llr_prox_limits(T):
+    rng, phi, mask, maps = random_problem(3, 1, 32, 32, 2, 8, 4, 1)
+    x = crandn(rng, 1, 1, 4, 32, 32)
+    with make_plan(T, phi, mask, maps, block=8) as p:
+        a = c64(x)
+        p.llr_prox(a, 0.0, 2, 3)
+        assert nrmse(host(a), x.astype(np.complex64)) < 1e-6
+        p.llr_prox(a, 1e6, 2, 3)
+        assert float(a.abs().max()) == 0.0
+
+
+def test_solve_single_slice_64x48(T):
+    """The 64 x 48, C=8, T=32, K=4, 10 %/echo, lambda=0.01, 50-iteration single slice,
+    per-echo (TE-form) input, against the oracle's FISTA."""
+    sh = synth.SINGLE_SLICE_64x48
+    phi, mask, maps, y = te_case(sh)
+    phi, maps = r32(phi, maps)
+    ys = y.astype(np.complex64).astype(np.complex128)
+    ref = O.fista(ys, "te", maps, mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
+    with make_plan(T, phi, mask, maps[None], block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed) as p:
+        got, res = p.solve(c64(y[None]), T.KSPACE_TE, residual=True)
+        got = host(got)[0]
+    e = nrmse(got, ref)
+    print("single-slice NRMSE", e)
+    assert e < SOLVE_TOL
+    assert np.all(np.isfinite(res)) and res[-1] < res[1]
+
+
+def test_solve_batch_ragged_two_maps(T):
+    """Several slices at once, partial LLR blocks (60 x 44, b = 8), M = 2, projected input."""
+    rng, phi, mask, maps = random_problem(11, 3, 60, 44, 4, 24, 4, 2, frac=0.2)
+    psi = O.space_time_kernel(mask, phi)
+    a_true = crandn(rng, 3, 2, 4, 60, 44) * 0.05
+    ytil = np.stack([O.apply_psi(O.fft2c(O.sense(a_true[s], maps[s])), psi) for s in range(3)])
+    ytil += 0.001 * crandn(rng, *ytil.shape) * (psi[..., 0, 0] > 0)
+    ys = ytil.astype(np.complex64).astype(np.complex128)
+    lam, b, it, seed = 0.02, 8, 30, 77
+    with make_plan(T, phi, mask, maps, block=b, lam=lam, iters=it, seed=seed) as p:
+        got = host(p.solve(c64(ytil), T.KSPACE_PROJ))
+    for s in range(3):
+        ref = O.fista(ys[s], "proj", maps[s], mask, phi, lam, b, it, seed)
+        assert nrmse(got[s], ref) < SOLVE_TOL
+
+
+def test_solve_no_shift_and_fixed_step(T):
+    rng, phi, mask, maps = random_problem(12, 2, 48, 40, 3, 16, 3, 1, frac=0.3)
+    y = crandn(rng, 2, 3, 16, 48, 40) * mask[None, None] * 0.1
+    ys = y.astype(np.complex64).astype(np.complex128)
+    with make_plan(T, phi, mask, maps, block=8, lam=0.05, iters=20, seed=5, step=0.7, flags=T.NO_SHIFT) as p:
+        assert abs(p.step - 0.7) < 1e-7
+        got = host(p.solve(c64(y), T.KSPACE_TE))
+    for s in range(2):
+        ref = O.fista(ys[s], "te", maps[s], mask, phi, 0.05, 8, 20, 5, step=0.7, shifts=False)
+        assert nrmse(got[s], ref) < SOLVE_TOL
+
+
+def test_solve_host_io_matches_device(T):
+    sh = synth.SINGLE_SLICE_64x48
+    phi, mask, maps, y = te_case(sh)
+    kw = dict(block=sh.block, lam=sh.lam, iters=10, seed=sh.seed)
+    with make_plan(T, phi, mask, maps[None], **kw) as p:
+        dev_out = host(p.solve(c64(y[None]), T.KSPACE_TE))
+    d = T.make_dims(64, 48, 8, 32, 4, flags=T.HOST_IO, **kw)
+    with T.Plan(d, phi.astype(np.float32), mask.astype(np.uint8), maps[None].astype(np.complex64)) as p:
+        host_out = p.solve(y[None].astype(np.complex64), T.KSPACE_TE)
+    assert np.array_equal(host_out.astype(np.complex128), dev_out)
+
+
+def test_solve_zero_iterations_and_empty_mask(T):
+    rng, phi, mask, maps = random_problem(13, 1, 32, 32, 2, 8, 4, 1)
+    zero_mask = np.zeros_like(mask)
+    with make_plan(T, phi, zero_mask, maps, block=8, lam=0.1, iters=5) as p:
+        assert p.step == 1.0
+        out = host(p.solve(c64(crandn(rng, 1, 2, 8, 32, 32)), T.KSPACE_TE))
+    assert np.all(out == 0)
+    with make_plan(T, phi, mask, maps, block=8, lam=0.1, iters=0) as p:
+        out = host(p.solve(c64(crandn(rng, 1, 2, 8, 32, 32)), T.KSPACE_TE))
+    assert np.all(out == 0)
+
+
+def test_solve_knee_slices_projected(T):
+    """Four slices of the 256 x 160, C = 12, T = 80, 5 %/echo knee scan (3D ellipsoid
+    phantom, projected input, lambda = 0.005, 100 iterations) against the oracle."""
+    sh = synth.KNEE_320x256x160
+    sl = [0, 101, 160, 319]
+    phi, mask, maps, ytil = proj_scan(sh, sl)
+    phi, maps = r32(phi, maps)
+    with make_plan(T, phi, mask, maps, block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed) as p:
+        got = host(p.solve(c64(ytil), T.KSPACE_PROJ))
+    ys = ytil.astype(np.complex64).astype(np.complex128)
+    for i in (0, 3):
+        ref = O.fista(ys[i], "proj", maps[i], mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
+        e = nrmse(got[i], ref)
+        print("knee slice", sl[i], "NRMSE", e)
+        assert e < SOLVE_TOL

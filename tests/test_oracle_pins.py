@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_1809_04195_gb300 import synth
+import t2sh_synth as synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
