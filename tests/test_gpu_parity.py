@@ -133,7 +133,7 @@ def test_step_matches_oracle(T):
 
 @pytest.mark.parametrize("ny,nz,b,sy,sz,M,K", [
     (64, 48, 8, 3, 5, 1, 4),
-    (60, 44, 8, 7, 2, 1, 4),    # partial blocks on both axes
+    (60, 36, 8, 7, 2, 1, 4),    # partial blocks on both axes
     (40, 24, 6, 5, 0, 2, 4),    # two map sets
     (48, 30, 8, 1, 6, 1, 6),    # K > 4
     (256, 160, 8, 0, 0, 1, 4),
@@ -183,10 +183,10 @@ def test_solve_single_slice_64x48(T):
 
 
 def test_solve_batch_ragged_two_maps(T):
-    """Several slices at once, partial LLR blocks (60 x 44, b = 8), M = 2, projected input."""
-    rng, phi, mask, maps = random_problem(11, 3, 60, 44, 4, 24, 4, 2, frac=0.2)
+    """Several slices at once, partial LLR blocks (60 x 36, b = 8), M = 2, projected input."""
+    rng, phi, mask, maps = random_problem(11, 3, 60, 36, 4, 24, 4, 2, frac=0.2)
     psi = O.space_time_kernel(mask, phi)
-    a_true = crandn(rng, 3, 2, 4, 60, 44) * 0.05
+    a_true = crandn(rng, 3, 2, 4, 60, 36) * 0.05
     ytil = np.stack([O.apply_psi(O.fft2c(O.sense(a_true[s], maps[s])), psi) for s in range(3)])
     ytil += 0.001 * crandn(rng, *ytil.shape) * (psi[..., 0, 0] > 0)
     ys = ytil.astype(np.complex64).astype(np.complex128)
