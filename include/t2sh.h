@@ -183,6 +183,33 @@ t2sh_status t2sh_workspace_bytes(const t2sh_dims* dims, size_t* bytes);
 t2sh_status t2sh_timing_enable(t2sh_plan_t plan, int32_t enable);
 t2sh_status t2sh_timing_read(t2sh_plan_t plan, int32_t kernel_class, int64_t* launches, double* ms);
 
+/*
+ * t2sh_normal_op_noalloc -- y = A^H A x like t2sh_normal_op, for callers that cannot
+ * allocate device memory (code running where cudaMalloc is not permitted, or an
+ * application that owns all device memory and forbids libraries to allocate).  It takes
+ * no plan and allocates nothing: the twiddle tables, Psi, the sign-folded maps and the
+ * per-coil intermediate live in one static device array of t2sh_noalloc_scratch_bytes()
+ * bytes (64 MiB) that every GPU loading the library holds until the process exits.
+ * The paper has no counterpart of this entry point.
+ *   dims  as for t2sh_plan (nslices, ny, nz, ncoils, nmaps, nbasis, nechoes used;
+ *         T2SH_HOST_IO not allowed)
+ *   phi [T][K] float32, mask [T][ny][nz] uint8, maps [S][C][M][ny][nz] complex,
+ *   x, y [S][M][K][ny][nz] complex (x == y allowed): all device pointers
+ *   stream  cudaStream_t to enqueue on (NULL: default stream)
+ * Sizes whose scratch (twiddles + Psi + maps + S*C*K*ny*nz complex, each rounded up to
+ * 256 bytes) exceeds the array are rejected with T2SH_EINVAL and a message.  The first
+ * call on a device resolves the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call reuses
+ * the same array and overwrites what the previous call left there, so calls that
+ * overlap on the GPU (different streams, or threads without ordering) race: serialise
+ * them.  Asynchronous on the stream.
+ */
+t2sh_status t2sh_normal_op_noalloc(const t2sh_dims* dims, const float* phi, const uint8_t* mask,
+                                   const void* maps, const void* x, void* y, void* stream);
+
+/* Size in bytes of the static scratch array behind t2sh_normal_op_noalloc. */
+size_t t2sh_noalloc_scratch_bytes(void);
+
 /* Message of the last failing call on this thread ("" if none).  Never NULL. */
 const char* t2sh_last_error(void);
 

@@ -138,6 +138,13 @@ t2sh_status validate(const t2sh_dims* d) {
 
 }  // namespace
 
+// Shared with the allocation-free entry point (t2sh_noalloc.cu).
+namespace t2sh {
+t2sh_status check_dims(const t2sh_dims* d) { return validate(d); }
+bool fft_plan_for(int n, FftPlan& p) { return make_fft_plan(n, p); }
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace t2sh
+
 struct t2sh_plan_s {
   t2sh_dims d{};
   cudaStream_t st = nullptr;

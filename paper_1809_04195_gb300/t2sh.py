@@ -72,6 +72,10 @@ def lib() -> ctypes.CDLL:
             f = getattr(L, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        L.t2sh_normal_op_noalloc.argtypes = [ctypes.POINTER(Dims), _vp, _vp, _vp, _vp, _vp, _vp]
+        L.t2sh_normal_op_noalloc.restype = ctypes.c_int
+        L.t2sh_noalloc_scratch_bytes.argtypes = []
+        L.t2sh_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.t2sh_last_error.argtypes = []
         L.t2sh_last_error.restype = ctypes.c_char_p
         L.t2sh_version.argtypes = []
@@ -84,7 +88,7 @@ def header_symbols() -> list[str]:
     """Function names declared in include/t2sh.h."""
     with open(HEADER) as f:
         txt = f.read()
-    return sorted(set(re.findall(r"^\s*(?:t2sh_status|const char\*|int32_t)\s+(t2sh_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:t2sh_status|const char\*|int32_t|size_t)\s+(t2sh_\w+)\s*\(", txt, re.M)))
 
 
 def _check(status: int):
@@ -128,6 +132,28 @@ def _ptr(t, dtype, shape, host: bool):
     if host == t.is_cuda:
         raise ValueError("host_io plans take host arrays; other plans take CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def normal_op_noalloc(dims: Dims, phi, mask, maps, x, out=None, stream=None):
+    """y = A^H A x without a plan and without any device allocation by the library
+    (scratch in a static device array; see include/t2sh.h).  CUDA tensors only."""
+    import torch
+    S, C, M, K, T, ny, nz = dims.nslices, dims.ncoils, dims.nmaps, dims.nbasis, dims.nechoes, dims.ny, dims.nz
+    vshape = (S, M, K, ny, nz)
+    if out is None:
+        out = torch.empty(vshape, dtype=torch.complex64, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().t2sh_normal_op_noalloc(ctypes.byref(dims), _ptr(phi, torch.float32, (T, K), False),
+                                        _ptr(mask, torch.uint8, (T, ny, nz), False),
+                                        _ptr(maps, torch.complex64, (S, C, M, ny, nz), False),
+                                        _ptr(x, torch.complex64, vshape, False), _ptr(out, torch.complex64, vshape, False),
+                                        ctypes.c_void_p(stream.cuda_stream)))
+    return out
+
+
+def noalloc_scratch_bytes() -> int:
+    return int(lib().t2sh_noalloc_scratch_bytes())
 
 
 class Plan:
