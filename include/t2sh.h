@@ -10,7 +10,9 @@
  * with FISTA (Sec. II.A, Sec. III.B).  The normal operator is applied through the
  * space-time kernel Psi(n) = Phi^T P(n) Phi (Sec. IV.B) and the LLR prox is the
  * singular-value soft threshold of non-overlapping b x b x K blocks of the randomly
- * circular-shifted coefficient images (Eq. 4, Sec. IV.C).
+ * circular-shifted coefficient images (Eq. 4, Sec. IV.C).  The SVT of each block is
+ * formed from its K x K Gram matrix (float32 accumulation) and a cyclic Jacobi
+ * eigendecomposition, in float32 unless T2SH_EIG_FP64 is set.
  *
  * Conventions shared by every entry point
  *   - Complex arrays are interleaved single precision (re, im), C order, last index
@@ -60,6 +62,7 @@ enum {
 /* t2sh_dims.flags */
 #define T2SH_NO_SHIFT 0x1u /* LLR without random shifts (fixed block grid)            */
 #define T2SH_HOST_IO 0x2u  /* array arguments of plan/solve are host pointers         */
+#define T2SH_EIG_FP64 0x4u /* LLR Gram eigendecomposition in float64 (default float32) */
 
 typedef struct {
   int32_t ny, nz;          /* slice matrix (phase encodes y, z); both even, 2/3/5-smooth,
@@ -76,7 +79,7 @@ typedef struct {
   float step;              /* > 0: FISTA step mu; <= 0: the plan computes mu = 1/L with
                               L = max_n lambda_max Psi(n) * max_p lambda_max S(p)^H S(p) */
   int32_t precision;       /* T2SH_FP32 (T2SH_MIXED_BF16: reserved, T2SH_EUNSUPPORTED)   */
-  uint32_t flags;          /* T2SH_NO_SHIFT | T2SH_HOST_IO                                */
+  uint32_t flags;          /* T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64                */
 } t2sh_dims;
 
 typedef struct t2sh_plan_s* t2sh_plan_t;

@@ -1,0 +1,376 @@
+// Size-specialised row and column passes for line lengths N = 16 * R1 (R1 in
+// {3, 4, 6, 8, 10, 12, 15, 16}: 48 ... 256, all slice sizes of the knee workloads).
+//
+// A line of N points is transformed by 16 threads in two register stages with one
+// shared-memory exchange, every index a compile-time constant:
+//   forward  [R1, 16]: thread j < 16 holds x[j + 16 r] (r < R1), DFT_R1; exchange;
+//                      thread j' < R1 holds Y[j' + R1 r] (r < 16), twiddle w^(r j'), DFT_16
+//                      -> X[j' + R1 k] (k < 16).
+//   inverse  [16, R1]: thread j' < R1 holds X[j' + R1 r], IDFT_16; exchange;
+//                      thread j < 16 holds Y[j + 16 r], twiddle w^(-r j), IDFT_R1
+//                      -> x[j + 16 k] (k < R1).
+// The row pass (kz) keeps each line in one half-warp, so global loads of a row are
+// 128-byte runs; the column pass (ky) puts the 8 columns of a tile on adjacent lanes.
+// Both stream their next inputs into shared memory with cp.async while computing.
+#include <algorithm>
+
+#include "t2sh_device.cuh"
+
+namespace t2sh {
+
+// odd row strides of the exchange layouts (bank-conflict-free half-warp access)
+template <int R1>
+struct Ex {
+  static constexpr int SF = (R1 % 2) ? R1 : R1 + 1;  // forward: [j < 16][r1 < R1]
+  static constexpr int SI = 17;                        // inverse: [j' < R1][r1 < 16]
+  static constexpr int LINE = (16 * SF > R1 * SI) ? 16 * SF : R1 * SI;
+};
+
+// ------------------------------------------------------------------------------------
+// Row pass.  CTA = (slice, band of RB rows), 16 x 4 x RB threads, thread
+// (j, line = k * RB + r).  K <= 4, M <= 2.  RB = 8, or 4 where 8 would not fit in
+// shared memory (N >= 240 or two map sets).
+// ------------------------------------------------------------------------------------
+template <int N, int MC>
+struct RowFastRB {
+  static constexpr int value = (N >= 240 || MC == 2) ? 4 : 8;
+};
+
+template <int N, int MODE, int MC, int kRowRB = RowFastRB<N, MC>::value>
+__global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* __restrict__ tw_g,
+                                                 const float2* __restrict__ maps, const float2* __restrict__ x,
+                                                 float2* __restrict__ t, float2* __restrict__ out) {
+  constexpr int R1 = N / 16;
+  constexpr int LINE = Ex<R1>::LINE;
+  constexpr int SF = Ex<R1>::SF;
+  extern __shared__ float2 smem[];
+  const int NN = g.ny * N, K = g.K, M = g.M;
+  const int s = blockIdx.y, y0 = blockIdx.x * kRowRB;
+  const int rb = min(kRowRB, g.ny - y0);
+  constexpr int NL = 4 * kRowRB;  // lines per CTA
+  const int j = threadIdx.x & 15;
+  const int L = threadIdx.x >> 4;  // line: k * RB + r
+  const int k = L / kRowRB, r = L - k * kRowRB;
+  const bool live = (k < K) && (r < rb);
+  // shared memory: twiddles | exchange [NL][LINE] | maps stage x2 [MC][RB][N] | t stage x2 [NL][N]
+  float2* tw = smem;
+  float2* ex = tw + N;
+  float2* mst = ex + NL * LINE;
+  float2* tst = mst + 2 * MC * kRowRB * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+
+  auto issue = [&](int c, int buf) {
+    const float2* mp = maps + ((long long)(s * g.C + c) * M) * NN + (long long)y0 * N;
+    float2* md = mst + buf * MC * kRowRB * N;
+    const int nm = M * rb * N / 2;
+    for (int e2 = threadIdx.x; e2 < nm; e2 += blockDim.x) {
+      const int e = 2 * e2;
+      const int m = e / (rb * N), rem = e - m * rb * N;
+      cp_async16(md + m * kRowRB * N + rem, mp + (long long)m * NN + rem);
+    }
+    if (MODE == ROW_ADJ) {
+      const float2* tp = t + ((long long)(s * g.C + c) * K) * NN + (long long)y0 * N;
+      float2* td = tst + buf * NL * N;
+      const int nt = K * rb * N / 2;
+      for (int e2 = threadIdx.x; e2 < nt; e2 += blockDim.x) {
+        const int e = 2 * e2;
+        const int kk = e / (rb * N), rem = e - kk * rb * N;
+        cp_async16(td + (kk * kRowRB) * N + rem, tp + (long long)kk * NN + rem);
+      }
+    }
+  };
+  issue(0, 0);
+  cp_async_commit();
+
+  float2 xr[MC][R1];   // ROW_FWD: x at z = j + 16 q
+  float2 acc[MC][16];  // ROW_ADJ: accumulated output at z = j + R1 q (j < R1)
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+      xr[m][q] = make_float2(0.f, 0.f);
+      if (MODE == ROW_FWD && live && m < M)
+        xr[m][q] = x[((long long)(s * M + m) * K + k) * NN + (long long)(y0 + r) * N + j + 16 * q];
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[m][q] = make_float2(0.f, 0.f);
+  }
+  float2* exl = ex + L * LINE;
+
+  for (int c = 0; c < g.C; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < g.C) issue(c + 1, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const float2* mrow = mst + buf * MC * kRowRB * N + r * N;
+    float2 a[R1];
+    if (MODE == ROW_FWD) {
+#pragma unroll
+      for (int q = 0; q < R1; ++q) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+          if (m < M) cfma(v, mrow[m * kRowRB * N + j + 16 * q], xr[m][q]);
+        a[q] = v;
+      }
+      dft_r<R1, false>(a);
+    } else {
+      const float2* trow = tst + buf * NL * N + L * N;
+#pragma unroll
+      for (int q = 0; q < R1; ++q) a[q] = trow[j + 16 * q];
+      dft_r<R1, true>(a);
+    }
+#pragma unroll
+    for (int q = 0; q < R1; ++q) exl[j * SF + q] = a[q];
+    __syncthreads();
+    if (j < R1 && live) {
+      float2 b[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
+#pragma unroll
+      for (int q = 1; q < 16; ++q) b[q] = (MODE == ROW_FWD) ? twiddle_mul<false>(b[q], tw[q * j]) : twiddle_mul<true>(b[q], tw[q * j]);
+      if (MODE == ROW_FWD) {
+        dft16<false>(b);
+        float2* tp = t + ((long long)(s * g.C + c) * K + k) * NN + (long long)(y0 + r) * N + j;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) tp[R1 * q] = b[q];
+      } else {
+        dft16<true>(b);
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+          if (m < M) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cfmac(acc[m][q], mrow[m * kRowRB * N + j + R1 * q], b[q]);
+          }
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if (MODE == ROW_ADJ && j < R1 && live) {
+#pragma unroll
+    for (int m = 0; m < MC; ++m)
+      if (m < M) {
+        float2* op = out + ((long long)(s * M + m) * K + k) * NN + (long long)(y0 + r) * N + j;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) op[R1 * q] = acc[m][q];
+      }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Column pass of the normal operator (DFT_y, Psi, IDFT_y), persistent over
+// (slice, coil, 8-column tile) tiles, 8 x 4 x 16 = 512 threads, thread (w, k, j),
+// warp = the 8 columns x 4 basis lines of one j.  Requires nz % 8 == 0, K <= 4.
+// ------------------------------------------------------------------------------------
+constexpr int kColW = 8;
+
+template <int N>
+__global__ void __launch_bounds__(512, 1) k_col_fast(Geom g, const float2* __restrict__ tw_g,
+                                                    const float* __restrict__ psi, float2* t, int ntz, int ntiles) {
+  constexpr int R1 = N / 16;
+  constexpr int LS = N + 1;             // exchange line stride (odd)
+  constexpr int PS = N * kColW + 8;     // staging plane stride (padded per basis line)
+  extern __shared__ float2 smem[];
+  const int nz = g.nz, NN = N * nz, K = g.K;
+  const int w = threadIdx.x & 7, k = (threadIdx.x >> 3) & 3, j = threadIdx.x >> 5;
+  float2* tw = smem;
+  float2* ex = tw + N;                  // [k][w][LS]
+  float2* st = ex + 4 * kColW * LS;     // 2 x [k][y][8] (+ pad)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+
+  auto issue = [&](int tile, int buf) {
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * kColW;
+    const float2* tb = t + (long long)sc * K * NN + z0;
+    float2* sd = st + buf * 4 * PS;
+    const int n16 = K * N * (kColW / 2);  // 16-byte copies
+    for (int e = threadIdx.x; e < n16; e += blockDim.x) {
+      const int w2 = (e & 3) * 2;
+      const int row = e >> 2;  // k * N + y
+      const int kk = row / N, y = row - kk * N;
+      cp_async16(sd + kk * PS + y * kColW + w2, tb + (long long)kk * NN + (long long)y * nz + w2);
+    }
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, 0);
+  cp_async_commit();
+  float2* exl = ex + (k * kColW + w) * LS;
+  const bool live = k < K;
+  int buf = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * kColW;
+    // forward stage A: x[j + 16 q] of column w, basis line k
+    if (live) {
+      const float2* sp = st + buf * 4 * PS + k * PS + w;
+      float2 a[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * kColW];
+      dft_r<R1, false>(a);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) exl[j * R1 + q] = a[q];
+    }
+    __syncthreads();
+    // forward stage B: X[j + R1 q]
+    if (live && j < R1) {
+      float2 b[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = exl[j + R1 * q];
+#pragma unroll
+      for (int q = 1; q < 16; ++q) b[q] = twiddle_mul<false>(b[q], tw[q * j]);
+      dft16<false>(b);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) exl[j + R1 * q] = b[q];
+    }
+    __syncthreads();
+    // space-time kernel: u_k = sum_l Psi_kl v_l at every point (ky, w) of the tile
+    for (int p = threadIdx.x; p < N * kColW; p += blockDim.x) {
+      const int pw = p & 7, ky = p >> 3;
+      const long long n = (long long)ky * nz + z0 + pw;
+      float2 v[4], u[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        v[l] = (l < K) ? ex[(l * kColW + pw) * LS + ky] : make_float2(0.f, 0.f);
+        u[l] = make_float2(0.f, 0.f);
+      }
+      int pp = 0;
+#pragma unroll
+      for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+        for (int b_ = a_; b_ < 4; ++b_)
+          if (b_ < K) {
+            const float ps = __ldg(psi + (long long)pp * NN + n);
+            ++pp;
+            u[a_].x = fmaf(ps, v[b_].x, u[a_].x);
+            u[a_].y = fmaf(ps, v[b_].y, u[a_].y);
+            if (b_ != a_) {
+              u[b_].x = fmaf(ps, v[a_].x, u[b_].x);
+              u[b_].y = fmaf(ps, v[a_].y, u[b_].y);
+            }
+          }
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        if (l < K) ex[(l * kColW + pw) * LS + ky] = u[l];
+    }
+    __syncthreads();
+    // inverse stage A': IDFT_16 of X[j + R1 q]
+    float2 b[16];
+    if (live && j < R1) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = exl[j + R1 * q];
+      dft16<true>(b);
+    }
+    __syncthreads();
+    if (live && j < R1) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) exl[j * 16 + q] = b[q];
+    }
+    __syncthreads();
+    // inverse stage B': y = j + 16 q, written straight back to global memory
+    if (live) {
+      float2 a[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) a[q] = twiddle_mul<true>(exl[j + 16 * q], tw[q * j]);
+      dft_r<R1, true>(a);
+      float2* ob = t + ((long long)sc * K + k) * NN + z0 + w;
+#pragma unroll
+      for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------
+// launchers: return cudaErrorNotSupported when the shape has no specialised kernel
+// ------------------------------------------------------------------------------------
+template <int N, int MODE, int MC>
+static size_t row_fast_smem() {
+  constexpr int R1 = N / 16, RB = RowFastRB<N, MC>::value, NL = 4 * RB;
+  return sizeof(float2) * ((size_t)N + NL * Ex<R1>::LINE + 2 * (size_t)MC * RB * N +
+                           (MODE == ROW_ADJ ? 2 * (size_t)NL * N : 0));
+}
+
+template <int N, int MODE, int MC>
+static cudaError_t row_fast_go(const Geom& g, const float2* tw, const float2* maps, const float2* x, float2* t,
+                               float2* out, cudaStream_t st) {
+  constexpr int RB = RowFastRB<N, MC>::value;
+  const size_t sm = row_fast_smem<N, MODE, MC>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_row_fast<N, MODE, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((g.ny + RB - 1) / RB, g.S);
+  k_row_fast<N, MODE, MC><<<grid, 64 * RB, sm, st>>>(g, tw, maps, x, t, out);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t row_fast_n(const Geom& g, RowMode mode, const float2* tw, const float2* maps, const float2* x,
+                              float2* t, float2* out, cudaStream_t st) {
+  if (mode == ROW_FWD)
+    return g.M == 1 ? row_fast_go<N, ROW_FWD, 1>(g, tw, maps, x, t, out, st)
+                    : row_fast_go<N, ROW_FWD, 2>(g, tw, maps, x, t, out, st);
+  return g.M == 1 ? row_fast_go<N, ROW_ADJ, 1>(g, tw, maps, x, t, out, st)
+                  : row_fast_go<N, ROW_ADJ, 2>(g, tw, maps, x, t, out, st);
+}
+
+cudaError_t launch_row_fast(const Geom& g, RowMode mode, const float2* tw_z, const float2* maps, const float2* x,
+                            float2* t, float2* out, cudaStream_t st) {
+  if (g.K > 4 || g.M > 2) return cudaErrorNotSupported;
+  switch (g.nz) {
+    case 48: return row_fast_n<48>(g, mode, tw_z, maps, x, t, out, st);
+    case 64: return row_fast_n<64>(g, mode, tw_z, maps, x, t, out, st);
+    case 96: return row_fast_n<96>(g, mode, tw_z, maps, x, t, out, st);
+    case 128: return row_fast_n<128>(g, mode, tw_z, maps, x, t, out, st);
+    case 160: return row_fast_n<160>(g, mode, tw_z, maps, x, t, out, st);
+    case 192: return row_fast_n<192>(g, mode, tw_z, maps, x, t, out, st);
+    case 240: return row_fast_n<240>(g, mode, tw_z, maps, x, t, out, st);
+    case 256: return row_fast_n<256>(g, mode, tw_z, maps, x, t, out, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <int N>
+static cudaError_t col_fast_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
+  const size_t sm = sizeof(float2) * ((size_t)N + 4 * kColW * (size_t)(N + 1) + 2 * 4 * (size_t)(N * kColW + 8));
+  static int nsm = 0;
+  if (!nsm) {
+    cudaError_t e = cudaFuncSetAttribute(k_col_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  const int ntz = g.nz / kColW;
+  const long long ntiles = (long long)g.S * g.C * ntz;
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ntiles, nsm);
+  k_col_fast<N><<<grid, 512, sm, st>>>(g, tw, psi, t, ntz, (int)ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
+  if (g.K > 4 || g.nz % kColW != 0) return cudaErrorNotSupported;
+  switch (g.ny) {
+    case 48: return col_fast_go<48>(g, tw_y, psi, t, st);
+    case 64: return col_fast_go<64>(g, tw_y, psi, t, st);
+    case 96: return col_fast_go<96>(g, tw_y, psi, t, st);
+    case 128: return col_fast_go<128>(g, tw_y, psi, t, st);
+    case 160: return col_fast_go<160>(g, tw_y, psi, t, st);
+    case 192: return col_fast_go<192>(g, tw_y, psi, t, st);
+    case 240: return col_fast_go<240>(g, tw_y, psi, t, st);
+    case 256: return col_fast_go<256>(g, tw_y, psi, t, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace t2sh

@@ -4,15 +4,16 @@
 //
 // One CTA per (slice, band of b shifted rows).  Per block (b x b pixels x K, per map
 // set) a warp forms the K x K Gram matrix G = X^H X with shuffle reductions; one
-// thread per block then eigendecomposes G = V diag(lambda) V^H in float64 (cyclic
-// Jacobi), sigma_i = sqrt(lambda_i), and forms W = V diag(max(1 - tau/sigma_i, 0)) V^H,
+// thread per block then eigendecomposes G = V diag(lambda) V^H (cyclic Jacobi, float32
+// by default, float64 on request), sigma_i = sqrt(lambda_i), and forms
+// W = V diag(max(1 - tau/sigma_i, 0)) V^H,
 // so that X W = U max(Sigma - tau, 0) V^H (since X V = U Sigma).  The FISTA variant
 // fuses the gradient step before the prox and the momentum update after it (Sec. II.A).
 #include "t2sh_device.cuh"
 
 namespace t2sh {
 
-template <int KC, bool FISTA>
+template <int KC, bool FISTA, typename ET>
 __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x, float2* z,
                                                 const float2* __restrict__ grad, const float2* __restrict__ aty) {
   extern __shared__ float2 smem[];
@@ -25,23 +26,28 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
   float2* wm = gs + (size_t)M * K * rb * nz;           // [nblk][KC][KC]
   float* gram = reinterpret_cast<float*>(wm + (size_t)nblk * KC * KC);  // [nblk][KC*KC]
 
-  // 1. gather the band (gradient step fused for FISTA)
-  const int nel = M * K * rb * nz;
-  for (int e = threadIdx.x; e < nel; e += kThreads) {
+  // 1. gather the band (gradient step fused for FISTA), two pixels per float4
+  const int nel2 = (M * K * rb * nz) >> 1;
+  for (int e2 = threadIdx.x; e2 < nel2; e2 += kThreads) {
+    const int e = 2 * e2;
     const int zz = e % nz;
     int rest = e / nz;
     const int r = rest % rb;
     rest /= rb;  // m * K + k
     const int y = (a.sy + band * b + r) % ny;
     const long long gi = ((long long)s * M * K + rest) * N + (long long)y * nz + zz;
-    float2 v;
+    float4 v;
     if (FISTA) {
-      const float2 zv = z[gi], gv = grad[gi], av = aty[gi];
-      v = make_float2(zv.x - a.mu * (gv.x - av.x), zv.y - a.mu * (gv.y - av.y));
+      const float4 zv = *reinterpret_cast<const float4*>(z + gi);
+      const float4 gv = *reinterpret_cast<const float4*>(grad + gi);
+      const float4 av = *reinterpret_cast<const float4*>(aty + gi);
+      v = make_float4(zv.x - a.mu * (gv.x - av.x), zv.y - a.mu * (gv.y - av.y), zv.z - a.mu * (gv.z - av.z),
+                      zv.w - a.mu * (gv.w - av.w));
     } else {
-      v = x[gi];
+      v = *reinterpret_cast<const float4*>(x + gi);
     }
-    gs[e] = v;
+    gs[e] = make_float2(v.x, v.y);
+    gs[e + 1] = make_float2(v.z, v.w);
   }
   __syncthreads();
 
@@ -87,22 +93,70 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
 
   // 3. eigendecomposition and threshold weights, one thread per block
   for (int blk = threadIdx.x; blk < nblk; blk += kThreads) {
-    double ar[KC][KC], ai[KC][KC], vr[KC][KC], vi[KC][KC];
+    ET ar[KC][KC], ai[KC][KC], vr[KC][KC], vi[KC][KC];
     const float* gp = gram + blk * KC * KC;
 #pragma unroll
     for (int k = 0; k < KC; ++k)
 #pragma unroll
       for (int l = 0; l < KC; ++l) {
-        if (k == l) { ar[k][l] = gp[k * KC + k]; ai[k][l] = 0.0; }
+        if (k == l) { ar[k][l] = gp[k * KC + k]; ai[k][l] = ET(0); }
         else if (k < l) { ar[k][l] = gp[k * KC + l]; ai[k][l] = gp[l * KC + k]; }
         else { ar[k][l] = gp[l * KC + k]; ai[k][l] = -gp[k * KC + l]; }
       }
-    herm_jacobi<double, KC>(ar, ai, vr, vi, 16);
-    double f[KC];
+    herm_jacobi<ET, KC>(ar, ai, vr, vi, 12);
+    // Rotations accumulated in float32 drift V away from orthonormal, and FISTA's
+    // momentum amplifies the resulting error in W; so re-orthonormalise V (modified
+    // Gram-Schmidt) and take each eigenvalue as the Rayleigh quotient v^H G v on the
+    // original Gram matrix.
 #pragma unroll
     for (int i = 0; i < KC; ++i) {
-      const double sig = sqrt(fmax(ar[i][i], 0.0));
-      f[i] = (sig > (double)a.tau) ? 1.0 - (double)a.tau / sig : 0.0;
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        ET pr = ET(0), pi = ET(0);  // v_j^H v_i
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          pr += vr[k][j] * vr[k][i] + vi[k][j] * vi[k][i];
+          pi += vr[k][j] * vi[k][i] - vi[k][j] * vr[k][i];
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          const ET nr = vr[k][i] - (pr * vr[k][j] - pi * vi[k][j]);
+          const ET ni = vi[k][i] - (pr * vi[k][j] + pi * vr[k][j]);
+          vr[k][i] = nr;
+          vi[k][i] = ni;
+        }
+      }
+      ET nn = ET(0);
+#pragma unroll
+      for (int k = 0; k < KC; ++k) nn += vr[k][i] * vr[k][i] + vi[k][i] * vi[k][i];
+      const ET inv = nn > ET(0) ? ET(1) / sqrt(nn) : ET(0);
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        vr[k][i] *= inv;
+        vi[k][i] *= inv;
+      }
+    }
+    ET f[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      // lambda_i = v_i^H G v_i, G Hermitian from the stored upper triangle
+      ET lam = ET(0);
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        ET gvr = ET(0), gvi = ET(0);  // (G v_i)_k
+#pragma unroll
+        for (int l = 0; l < KC; ++l) {
+          ET gr_, gi_;
+          if (k == l) { gr_ = gp[k * KC + k]; gi_ = ET(0); }
+          else if (k < l) { gr_ = gp[k * KC + l]; gi_ = gp[l * KC + k]; }
+          else { gr_ = gp[l * KC + k]; gi_ = -gp[k * KC + l]; }
+          gvr += gr_ * vr[l][i] - gi_ * vi[l][i];
+          gvi += gr_ * vi[l][i] + gi_ * vr[l][i];
+        }
+        lam += vr[k][i] * gvr + vi[k][i] * gvi;
+      }
+      const ET sig = sqrt(lam > ET(0) ? lam : ET(0));
+      f[i] = (sig > (ET)a.tau) ? ET(1) - (ET)a.tau / sig : ET(0);
     }
     float2* w = wm + (size_t)blk * KC * KC;
 #pragma unroll
@@ -110,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
 #pragma unroll
       for (int k = 0; k < KC; ++k) {
         // W_lk = sum_i V_li f_i conj(V_ki)
-        double wr = 0.0, wi = 0.0;
+        ET wr = ET(0), wi = ET(0);
 #pragma unroll
         for (int i = 0; i < KC; ++i) {
           wr += f[i] * (vr[l][i] * vr[k][i] + vi[l][i] * vi[k][i]);
@@ -166,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
   }
 }
 
-template <int KC, bool FISTA>
+template <int KC, bool FISTA, typename ET>
 static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                           const float2* aty, cudaStream_t st) {
   const int nbz = (g.nz + a.b - 1) / a.b;
@@ -175,20 +229,26 @@ static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* 
                     sizeof(float) * (size_t)nblk * KC * KC;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_llr<KC, FISTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_llr<KC, FISTA, ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((g.ny + a.b - 1) / a.b, g.S);
-  k_llr<KC, FISTA><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty);
+  k_llr<KC, FISTA, ET><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty);
   return cudaGetLastError();
 }
 
 cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                        const float2* aty, cudaStream_t st) {
   const bool fista = (z != nullptr);
-  if (g.K <= 4) return fista ? llr_go<4, true>(g, a, x, z, grad, aty, st) : llr_go<4, false>(g, a, x, z, grad, aty, st);
-  return fista ? llr_go<8, true>(g, a, x, z, grad, aty, st) : llr_go<8, false>(g, a, x, z, grad, aty, st);
+  if (a.eig64) {
+    if (g.K <= 4)
+      return fista ? llr_go<4, true, double>(g, a, x, z, grad, aty, st) : llr_go<4, false, double>(g, a, x, z, grad, aty, st);
+    return fista ? llr_go<8, true, double>(g, a, x, z, grad, aty, st) : llr_go<8, false, double>(g, a, x, z, grad, aty, st);
+  }
+  if (g.K <= 4)
+    return fista ? llr_go<4, true, float>(g, a, x, z, grad, aty, st) : llr_go<4, false, float>(g, a, x, z, grad, aty, st);
+  return fista ? llr_go<8, true, float>(g, a, x, z, grad, aty, st) : llr_go<8, false, float>(g, a, x, z, grad, aty, st);
 }
 
 size_t llr_smem_bytes(const Geom& g, int b) {

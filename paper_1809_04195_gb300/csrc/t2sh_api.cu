@@ -126,7 +126,7 @@ t2sh_status validate(const t2sh_dims* d) {
     set_err("precision %d not implemented", d->precision);
     return T2SH_EUNSUPPORTED;
   }
-  T2SH_REQ((d->flags & ~(T2SH_NO_SHIFT | T2SH_HOST_IO)) == 0, "unknown flag bits");
+  T2SH_REQ((d->flags & ~(T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64)) == 0, "unknown flag bits");
   Geom g{};
   g.M = d->nmaps; g.K = d->nbasis; g.nz = d->nz;
   if (llr_smem_bytes(g, d->block) > 200 * 1024) {
@@ -448,6 +448,7 @@ t2sh_status t2sh_llr_prox(t2sh_plan_t p, void* x, float tau, int32_t sy, int32_t
   T2SH_REQ(sy >= 0 && sz >= 0 && sy < p->d.block && sz < p->d.block, "shift must be in [0, block)");
   FistaArgs a{};
   a.mu = 0.f; a.tau = tau; a.beta = 0.f; a.sy = sy; a.sz = sz; a.b = p->d.block; a.res = nullptr;
+  a.eig64 = (p->d.flags & T2SH_EIG_FP64) ? 1 : 0;
   KTimer k(p, KC_LLR);
   T2SH_CK(launch_llr(p->g, a, static_cast<float2*>(x), nullptr, nullptr, nullptr, p->st));
   return T2SH_OK;
@@ -496,6 +497,7 @@ t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* a
     a.sy = p->shifts[2 * it];
     a.sz = p->shifts[2 * it + 1];
     a.b = d.block;
+    a.eig64 = (d.flags & T2SH_EIG_FP64) ? 1 : 0;
     a.res = residual_out ? p->res + 2 * it : nullptr;
     { KTimer k(p, KC_LLR); T2SH_CK(launch_llr(p->g, a, p->x, p->z, p->grad, p->aty, p->st)); }
     tk = tn;

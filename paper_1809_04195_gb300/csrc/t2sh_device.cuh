@@ -143,14 +143,54 @@ __device__ __forceinline__ void dft16(float2* v) {
   }
 }
 
+// Good-Thomas (prime factor) DFT of length A*B with gcd(A, B) = 1: with input map
+// n = (B n1 + A n2) mod AB and output map k = (B eA k1 + A eB k2) mod AB, where
+// eA = B^-1 mod A and eB = A^-1 mod B, the length-AB DFT is a 2D A x B DFT with no
+// twiddle factors.  Every index is a compile-time constant.
+constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return 1;
+}
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2* v);
+
+template <int A, int B, bool INV>
+__device__ __forceinline__ void dft_pfa(float2* v) {
+  constexpr int N = A * B;
+  constexpr int eA = inv_mod(B % A, A), eB = inv_mod(A % B, B);
+  float2 c[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) c[n2][n1] = v[(B * n1 + A * n2) % N];
+    dft_r<A, INV>(c[n2]);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    float2 d[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) d[n2] = c[n2][k1];
+    dft_r<B, INV>(d);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[(B * eA * k1 + A * eB * k2) % N] = d[k2];
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2* v) {
-  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) dft2<INV>(v[0], v[1]);
   else if constexpr (R == 3) dft3<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
   else if constexpr (R == 5) dft5<INV>(v);
+  else if constexpr (R == 6) dft_pfa<2, 3, INV>(v);
   else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 10) dft_pfa<2, 5, INV>(v);
+  else if constexpr (R == 12) dft_pfa<4, 3, INV>(v);
+  else if constexpr (R == 15) dft_pfa<3, 5, INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
+  else static_assert(R == 2, "unsupported radix");
 }
 
 // ---------------------------------------------------------------------------------
@@ -310,6 +350,23 @@ __device__ __forceinline__ void herm_jacobi(T (&ar)[K][K], T (&ai)[K][K], T (&vr
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, completion per commit group).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // sign (-1)^(a) as float

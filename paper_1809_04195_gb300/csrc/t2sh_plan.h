@@ -54,6 +54,7 @@ struct FistaArgs {
   float beta;    // (t_k - 1) / t_{k+1}
   int sy, sz;    // LLR shift of this iteration
   int b;         // block edge
+  int eig64;     // 1: eigendecomposition in float64, 0: float32
   double* res;   // nullable: accumulates {sum |x_{k+1} - x_k|^2, sum |x_{k+1}|^2}
 };
 
@@ -71,6 +72,11 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
                        const float* phi, const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st);
 cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                        const float2* aty, cudaStream_t st);
+
+// size-specialised passes (k_fft_fast.cu); cudaErrorNotSupported when the shape has none
+cudaError_t launch_row_fast(const Geom& g, RowMode mode, const float2* tw_z, const float2* maps, const float2* x,
+                            float2* t, float2* out, cudaStream_t st);
+cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 
 int row_rows_per_cta(const Geom& g);
 int col_cols_per_cta(const Geom& g);

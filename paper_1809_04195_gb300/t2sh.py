@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "t2sh.h")
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, EBUSY = range(7)
 FP32, MIXED_BF16 = 0, 1
 KSPACE_TE, KSPACE_PROJ = 0, 1
-NO_SHIFT, HOST_IO = 0x1, 0x2
+NO_SHIFT, HOST_IO, EIG_FP64 = 0x1, 0x2, 0x4
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "ETIMEOUT", 6: "EBUSY"}
 
 

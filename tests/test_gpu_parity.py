@@ -83,6 +83,9 @@ SHAPES = [
     (2, 60, 36, 4, 10, 3, 1),   # radix-3/5 passes, K < 4
     (2, 48, 30, 2, 14, 6, 1),   # K > 4 path
     (1, 256, 160, 2, 16, 4, 1),  # the knee slice matrix
+    (1, 240, 128, 3, 12, 4, 1),  # size-specialised passes with 4-row bands
+    (1, 192, 192, 2, 12, 4, 2),  # two map sets on the specialised passes
+    (2, 96, 64, 2, 8, 2, 1),     # K = 2 on the specialised passes
 ]
 
 
@@ -165,15 +168,18 @@ def test_llr_prox_limits(T):
         assert float(a.abs().max()) == 0.0
 
 
-def test_solve_single_slice_64x48(T):
+@pytest.mark.parametrize("eig64", [False, True])
+def test_solve_single_slice_64x48(T, eig64):
     """The 64 x 48, C=8, T=32, K=4, 10 %/echo, lambda=0.01, 50-iteration single slice,
-    per-echo (TE-form) input, against the oracle's FISTA."""
+    per-echo (TE-form) input, against the oracle's FISTA; float32 and float64 LLR
+    eigendecompositions."""
     sh = synth.SINGLE_SLICE_64x48
     phi, mask, maps, y = te_case(sh)
     phi, maps = r32(phi, maps)
     ys = y.astype(np.complex64).astype(np.complex128)
     ref = O.fista(ys, "te", maps, mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
-    with make_plan(T, phi, mask, maps[None], block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed) as p:
+    with make_plan(T, phi, mask, maps[None], block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed,
+                   flags=T.EIG_FP64 if eig64 else 0) as p:
         got, res = p.solve(c64(y[None]), T.KSPACE_TE, residual=True)
         got = host(got)[0]
     e = nrmse(got, ref)
