@@ -266,6 +266,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     from paper_1809_04195_gb300 import t2sh
+    from paper_1809_04195_gb300.dist import max_over_ranks, sum_over_ranks
 
     sh, S, iters = workload(args)
     phi_d, mask_d, maps_d, ytil_d = make_inputs(sh, S, torch, t2sh, dev)
@@ -304,12 +305,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * units * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(t0.elapsed_time(t1))
+    value = sum_over_ranks(units * args.steps) / (ms / 1000.0)
 
     # e2e: the same reconstruction through host buffers (pinned), copies inside the timing
     e2e = None
@@ -336,13 +333,9 @@ def run_ours(args):
         for _ in range(args.steps):
             hstep()
         torch.cuda.synchronize()
-        es = time.perf_counter() - e0
-        if world > 1:
-            tt = torch.tensor([es], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            es = float(tt.item())
+        es = max_over_ranks(time.perf_counter() - e0)
         h2d = hphi.nbytes + hmask.nbytes + hmaps.numel() * 8 + hy.numel() * 8
-        e2e = {"value": world * units * args.steps / es, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": sum_over_ranks(units * args.steps) / es, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hout.numel() * 8), "full_scan_s": es / args.steps,
                "api": "t2sh_plan + t2sh_solve with T2SH_HOST_IO (pinned host buffers)"}
         del hmaps, hy, hout

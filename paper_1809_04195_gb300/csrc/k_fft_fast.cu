@@ -28,15 +28,16 @@ struct Ex {
 
 // ------------------------------------------------------------------------------------
 // Row pass.  CTA = (slice, band of RB rows), 16 x 4 x RB threads, thread
-// (j, line = k * RB + r).  K <= 4, M <= 2.  RB = 8, or 4 where 8 would not fit in
-// shared memory (N >= 240 or two map sets).
+// (j, line = k * RB + r).  K <= 4, M <= 2.  RB = 8 for the forward pass; 4 for the
+// adjoint pass (its double-buffered t rows) and wherever 8 would not fit in shared
+// memory (N >= 240 or two map sets).
 // ------------------------------------------------------------------------------------
-template <int N, int MC>
+template <int N, int MC, int MODE>
 struct RowFastRB {
-  static constexpr int value = (N >= 240 || MC == 2) ? 4 : 8;
+  static constexpr int value = (N >= 240 || MC == 2 || MODE == ROW_ADJ) ? 4 : 8;
 };
 
-template <int N, int MODE, int MC, int kRowRB = RowFastRB<N, MC>::value>
+template <int N, int MODE, int MC, int kRowRB = RowFastRB<N, MC, MODE>::value>
 __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* __restrict__ tw_g,
                                                  const float2* __restrict__ maps, const float2* __restrict__ x,
                                                  float2* __restrict__ t, float2* __restrict__ out) {
@@ -161,60 +162,84 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
 
 // ------------------------------------------------------------------------------------
 // Column pass of the normal operator (DFT_y, Psi, IDFT_y), persistent over
-// (slice, coil, 8-column tile) tiles, 8 x 4 x 16 = 512 threads, thread (w, k, j),
-// warp = the 8 columns x 4 basis lines of one j.  Requires nz % 8 == 0, K <= 4.
+// (slice, coil, W-column tile) tiles, W x 4 x 16 threads, thread (w, k, j).
+// The tile's columns are staged in shared memory by cp.async, refilled for the next
+// tile as soon as the forward stage A has consumed them; the tile's block of Psi
+// (P x N x W floats) is staged the same way right after the Psi step.  With W = 4 a
+// CTA uses about 106 KB, so two CTAs share an SM.  Requires nz % W == 0, K <= 4.
 // ------------------------------------------------------------------------------------
-constexpr int kColW = 8;
+template <int N, int W>
+struct ColFast {
+  static constexpr int R1 = N / 16;
+  static constexpr int LS = N + 1;         // exchange line stride (odd)
+  static constexpr int PS = N * W + W;     // staging plane stride (pad W: basis lines on other banks)
+  static constexpr int THREADS = W * 64;
+  static constexpr size_t smem(int P) {
+    return sizeof(float2) * ((size_t)N + 4 * W * (size_t)LS + 4 * (size_t)PS) + sizeof(float) * (size_t)P * N * W;
+  }
+};
 
-template <int N>
-__global__ void __launch_bounds__(512, 1) k_col_fast(Geom g, const float2* __restrict__ tw_g,
+template <int N, int W>
+__global__ void __launch_bounds__(W * 64) k_col_fast(Geom g, const float2* __restrict__ tw_g,
                                                     const float* __restrict__ psi, float2* t, int ntz, int ntiles) {
-  constexpr int R1 = N / 16;
-  constexpr int LS = N + 1;             // exchange line stride (odd)
-  constexpr int PS = N * kColW + 8;     // staging plane stride (padded per basis line)
+  using CF = ColFast<N, W>;
+  constexpr int R1 = CF::R1, LS = CF::LS, PS = CF::PS;
   extern __shared__ float2 smem[];
-  const int nz = g.nz, NN = N * nz, K = g.K;
-  const int w = threadIdx.x & 7, k = (threadIdx.x >> 3) & 3, j = threadIdx.x >> 5;
+  const int nz = g.nz, NN = N * nz, K = g.K, P = g.P;
+  const int w = threadIdx.x % W, k = (threadIdx.x / W) & 3, j = threadIdx.x / (4 * W);
   float2* tw = smem;
-  float2* ex = tw + N;                  // [k][w][LS]
-  float2* st = ex + 4 * kColW * LS;     // 2 x [k][y][8] (+ pad)
+  float2* ex = tw + N;                                      // [k][w][LS]
+  float2* st = ex + 4 * W * LS;                             // [k][y][W] (+ pad per k)
+  float* ps = reinterpret_cast<float*>(st + 4 * PS);         // [p][y][W]
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
 
-  auto issue = [&](int tile, int buf) {
-    const int sc = tile / ntz, z0 = (tile - sc * ntz) * kColW;
+  auto issue_t = [&](int tile) {
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
     const float2* tb = t + (long long)sc * K * NN + z0;
-    float2* sd = st + buf * 4 * PS;
-    const int n16 = K * N * (kColW / 2);  // 16-byte copies
+    const int n16 = K * N * (W / 2);  // 16-byte copies
     for (int e = threadIdx.x; e < n16; e += blockDim.x) {
-      const int w2 = (e & 3) * 2;
-      const int row = e >> 2;  // k * N + y
+      const int w2 = (e % (W / 2)) * 2;
+      const int row = e / (W / 2);  // k * N + y
       const int kk = row / N, y = row - kk * N;
-      cp_async16(sd + kk * PS + y * kColW + w2, tb + (long long)kk * NN + (long long)y * nz + w2);
+      cp_async16(st + kk * PS + y * W + w2, tb + (long long)kk * NN + (long long)y * nz + w2);
+    }
+  };
+  auto issue_psi = [&](int tile) {
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
+    const int n16 = P * N * (W / 4);  // 16-byte copies of 4 floats
+    for (int e = threadIdx.x; e < n16; e += blockDim.x) {
+      const int w4 = (e % (W / 4)) * 4;
+      const int row = e / (W / 4);  // p * N + y
+      const int pp = row / N, y = row - pp * N;
+      cp_async16(ps + (pp * N + y) * W + w4, psi + (long long)pp * NN + (long long)y * nz + z0 + w4);
     }
   };
   int tile = blockIdx.x;
-  if (tile < ntiles) issue(tile, 0);
+  if (tile < ntiles) {
+    issue_t(tile);
+    issue_psi(tile);
+  }
   cp_async_commit();
-  float2* exl = ex + (k * kColW + w) * LS;
+  float2* exl = ex + (k * W + w) * LS;
   const bool live = k < K;
-  int buf = 0;
   for (; tile < ntiles; tile += gridDim.x) {
-    if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, buf ^ 1);
-    cp_async_commit();
-    cp_async_wait<1>();
+    const int nxt = tile + gridDim.x;
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
+    cp_async_wait<0>();
     __syncthreads();
-    const int sc = tile / ntz, z0 = (tile - sc * ntz) * kColW;
     // forward stage A: x[j + 16 q] of column w, basis line k
     if (live) {
-      const float2* sp = st + buf * 4 * PS + k * PS + w;
+      const float2* sp = st + k * PS + w;
       float2 a[R1];
 #pragma unroll
-      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * kColW];
+      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * W];
       dft_r<R1, false>(a);
 #pragma unroll
       for (int q = 0; q < R1; ++q) exl[j * R1 + q] = a[q];
     }
     __syncthreads();
+    if (nxt < ntiles) issue_t(nxt);  // the staging area is free again
+    cp_async_commit();
     // forward stage B: X[j + R1 q]
     if (live && j < R1) {
       float2 b[16];
@@ -227,36 +252,45 @@ __global__ void __launch_bounds__(512, 1) k_col_fast(Geom g, const float2* __res
       for (int q = 0; q < 16; ++q) exl[j + R1 * q] = b[q];
     }
     __syncthreads();
-    // space-time kernel: u_k = sum_l Psi_kl v_l at every point (ky, w) of the tile
-    for (int p = threadIdx.x; p < N * kColW; p += blockDim.x) {
-      const int pw = p & 7, ky = p >> 3;
-      const long long n = (long long)ky * nz + z0 + pw;
-      float2 v[4], u[4];
+    // space-time kernel: u_k = sum_l Psi_kl v_l; a thread takes 4 adjacent points of row ky
+    for (int pg = threadIdx.x; pg < N * (W / 4); pg += blockDim.x) {
+      const int ky = pg % N, c0 = (pg / N) * 4;
+      float2 v[4][4], u[4][4];
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        v[l] = (l < K) ? ex[(l * kColW + pw) * LS + ky] : make_float2(0.f, 0.f);
-        u[l] = make_float2(0.f, 0.f);
-      }
+      for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          v[l][c] = (l < K) ? ex[(l * W + c0 + c) * LS + ky] : make_float2(0.f, 0.f);
+          u[l][c] = make_float2(0.f, 0.f);
+        }
       int pp = 0;
 #pragma unroll
       for (int a_ = 0; a_ < 4; ++a_)
 #pragma unroll
         for (int b_ = a_; b_ < 4; ++b_)
           if (b_ < K) {
-            const float ps = __ldg(psi + (long long)pp * NN + n);
+            const float4 q4 = *reinterpret_cast<const float4*>(ps + (pp * N + ky) * W + c0);
+            const float pv[4] = {q4.x, q4.y, q4.z, q4.w};
             ++pp;
-            u[a_].x = fmaf(ps, v[b_].x, u[a_].x);
-            u[a_].y = fmaf(ps, v[b_].y, u[a_].y);
-            if (b_ != a_) {
-              u[b_].x = fmaf(ps, v[a_].x, u[b_].x);
-              u[b_].y = fmaf(ps, v[a_].y, u[b_].y);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              u[a_][c].x = fmaf(pv[c], v[b_][c].x, u[a_][c].x);
+              u[a_][c].y = fmaf(pv[c], v[b_][c].y, u[a_][c].y);
+              if (b_ != a_) {
+                u[b_][c].x = fmaf(pv[c], v[a_][c].x, u[b_][c].x);
+                u[b_][c].y = fmaf(pv[c], v[a_][c].y, u[b_][c].y);
+              }
             }
           }
 #pragma unroll
       for (int l = 0; l < 4; ++l)
-        if (l < K) ex[(l * kColW + pw) * LS + ky] = u[l];
+        if (l < K)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) ex[(l * W + c0 + c) * LS + ky] = u[l][c];
     }
     __syncthreads();
+    if (nxt < ntiles) issue_psi(nxt);  // the Psi block is free again
+    cp_async_commit();
     // inverse stage A': IDFT_16 of X[j + R1 q]
     float2 b[16];
     if (live && j < R1) {
@@ -280,8 +314,6 @@ __global__ void __launch_bounds__(512, 1) k_col_fast(Geom g, const float2* __res
 #pragma unroll
       for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
     }
-    __syncthreads();
-    buf ^= 1;
   }
   cp_async_wait<0>();
 }
@@ -289,9 +321,10 @@ __global__ void __launch_bounds__(512, 1) k_col_fast(Geom g, const float2* __res
 // ------------------------------------------------------------------------------------
 // launchers: return cudaErrorNotSupported when the shape has no specialised kernel
 // ------------------------------------------------------------------------------------
+constexpr int kColW = 8;  // columns per tile of the column pass
 template <int N, int MODE, int MC>
 static size_t row_fast_smem() {
-  constexpr int R1 = N / 16, RB = RowFastRB<N, MC>::value, NL = 4 * RB;
+  constexpr int R1 = N / 16, RB = RowFastRB<N, MC, MODE>::value, NL = 4 * RB;
   return sizeof(float2) * ((size_t)N + NL * Ex<R1>::LINE + 2 * (size_t)MC * RB * N +
                            (MODE == ROW_ADJ ? 2 * (size_t)NL * N : 0));
 }
@@ -299,7 +332,7 @@ static size_t row_fast_smem() {
 template <int N, int MODE, int MC>
 static cudaError_t row_fast_go(const Geom& g, const float2* tw, const float2* maps, const float2* x, float2* t,
                                float2* out, cudaStream_t st) {
-  constexpr int RB = RowFastRB<N, MC>::value;
+  constexpr int RB = RowFastRB<N, MC, MODE>::value;
   const size_t sm = row_fast_smem<N, MODE, MC>();
   static bool attr = false;
   if (!attr) {
@@ -339,36 +372,43 @@ cudaError_t launch_row_fast(const Geom& g, RowMode mode, const float2* tw_z, con
   }
 }
 
-template <int N>
+template <int N, int W>
 static cudaError_t col_fast_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
-  const size_t sm = sizeof(float2) * ((size_t)N + 4 * kColW * (size_t)(N + 1) + 2 * 4 * (size_t)(N * kColW + 8));
-  static int nsm = 0;
+  using CF = ColFast<N, W>;
+  const size_t sm = CF::smem(g.P);
+  static int nsm = 0, per = 0;
   if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_col_fast<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CF::smem(10));
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_fast<N, W>, CF::THREADS, CF::smem(10))) !=
+        cudaSuccess)
+      return e;
+    if (per < 1) per = 1;
   }
-  const int ntz = g.nz / kColW;
+  const int ntz = g.nz / W;
   const long long ntiles = (long long)g.S * g.C * ntz;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>(ntiles, nsm);
-  k_col_fast<N><<<grid, 512, sm, st>>>(g, tw, psi, t, ntz, (int)ntiles);
+  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * per);
+  k_col_fast<N, W><<<grid, CF::THREADS, sm, st>>>(g, tw, psi, t, ntz, (int)ntiles);
   return cudaGetLastError();
 }
 
 cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
-  if (g.K > 4 || g.nz % kColW != 0) return cudaErrorNotSupported;
+  constexpr int W = kColW;
+  if (g.K > 4 || g.nz % W != 0) return cudaErrorNotSupported;
   switch (g.ny) {
-    case 48: return col_fast_go<48>(g, tw_y, psi, t, st);
-    case 64: return col_fast_go<64>(g, tw_y, psi, t, st);
-    case 96: return col_fast_go<96>(g, tw_y, psi, t, st);
-    case 128: return col_fast_go<128>(g, tw_y, psi, t, st);
-    case 160: return col_fast_go<160>(g, tw_y, psi, t, st);
-    case 192: return col_fast_go<192>(g, tw_y, psi, t, st);
-    case 240: return col_fast_go<240>(g, tw_y, psi, t, st);
-    case 256: return col_fast_go<256>(g, tw_y, psi, t, st);
+    case 48: return col_fast_go<48, W>(g, tw_y, psi, t, st);
+    case 64: return col_fast_go<64, W>(g, tw_y, psi, t, st);
+    case 96: return col_fast_go<96, W>(g, tw_y, psi, t, st);
+    case 128: return col_fast_go<128, W>(g, tw_y, psi, t, st);
+    case 160: return col_fast_go<160, W>(g, tw_y, psi, t, st);
+    case 192: return col_fast_go<192, W>(g, tw_y, psi, t, st);
+    case 240: return col_fast_go<240, W>(g, tw_y, psi, t, st);
+    case 256: return col_fast_go<256, W>(g, tw_y, psi, t, st);
     default: return cudaErrorNotSupported;
   }
 }

@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
         else if (k < l) { ar[k][l] = gp[k * KC + l]; ai[k][l] = gp[l * KC + k]; }
         else { ar[k][l] = gp[l * KC + k]; ai[k][l] = -gp[k * KC + l]; }
       }
-    herm_jacobi<ET, KC>(ar, ai, vr, vi, 12);
+    herm_jacobi<ET, KC>(ar, ai, vr, vi, 5);
+    // Five cyclic sweeps converge a 4 x 4 Hermitian matrix to working precision.
     // Rotations accumulated in float32 drift V away from orthonormal, and FISTA's
     // momentum amplifies the resulting error in W; so re-orthonormalise V (modified
     // Gram-Schmidt) and take each eigenvalue as the Rayleigh quotient v^H G v on the
@@ -175,8 +176,11 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
   }
   __syncthreads();
 
-  // 4. X' = X W, then FISTA momentum; write back
-  double d2 = 0.0, x2 = 0.0;
+  // 4. X' = X W, then FISTA momentum; write back.  The optional convergence monitor sums
+  // |x_{k+1} - x_k|^2 and |x_{k+1}|^2 in float32 per thread (float64 only for the
+  // cross-thread reduction: the float64 pipe is a small fraction of float32 on GB300).
+  const bool want_res = FISTA && a.res != nullptr;
+  float d2 = 0.f, x2 = 0.f;
   const int npx = M * rb * nz;
   for (int e = threadIdx.x; e < npx; e += kThreads) {
     const int zz = e % nz;
@@ -200,22 +204,25 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
           const float2 xo = x[gi];
           const float2 dx = csub(o, xo);
           z[gi] = make_float2(o.x + a.beta * dx.x, o.y + a.beta * dx.y);
-          d2 += (double)dx.x * dx.x + (double)dx.y * dx.y;
-          x2 += (double)o.x * o.x + (double)o.y * o.y;
+          if (want_res) {
+            d2 = fmaf(dx.x, dx.x, fmaf(dx.y, dx.y, d2));
+            x2 = fmaf(o.x, o.x, fmaf(o.y, o.y, x2));
+          }
         }
         x[gi] = o;
       }
     }
   }
-  if (FISTA && a.res != nullptr) {
+  if (want_res) {
+    double dd = d2, xx = x2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-      x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+      xx += __shfl_xor_sync(0xffffffffu, xx, o);
     }
     if (lane == 0) {
-      atomicAdd(a.res, d2);
-      atomicAdd(a.res + 1, x2);
+      atomicAdd(a.res, dd);
+      atomicAdd(a.res + 1, xx);
     }
   }
 }
