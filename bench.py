@@ -28,7 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "slice-iterations/s (T2 Shuffling FISTA PICS solve, full scan)"
 UNIT = "slice-iter/s"
-KERNEL_FILES = ["t2sh_device.cuh", "t2sh_plan.h", "k_fft.cu", "k_fft_fast.cu", "k_llr.cu", "k_prep.cu", "t2sh_api.cu"]
+KERNEL_FILES = ["t2sh_device.cuh", "t2sh_plan.h", "k_fft.cu", "k_fft_fast.cu", "k_fused.cu", "k_llr.cu", "k_prep.cu",
+                "t2sh_api.cu"]
 
 
 def parse():
@@ -173,7 +174,8 @@ def algorithmic_bytes(S, C, M, K, N):
     vec = S * M * K * N * 8
     t = S * C * K * N * 8
     maps = S * C * M * N * 8
-    return {"row_fwd": vec + maps + t, "row_adj": t + maps + vec, "col": 2 * t, "llr": 6 * vec}
+    return {"row_fwd": vec + maps + t, "row_adj": t + maps + vec, "col": 2 * t, "llr": 6 * vec,
+            "band": 2 * t + maps + 5 * vec}
 
 
 def measured_peaks():

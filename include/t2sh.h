@@ -63,6 +63,10 @@ enum {
 #define T2SH_NO_SHIFT 0x1u /* LLR without random shifts (fixed block grid)            */
 #define T2SH_HOST_IO 0x2u  /* array arguments of plan/solve are host pointers         */
 #define T2SH_EIG_FP64 0x4u /* LLR Gram eigendecomposition in float64 (default float32) */
+#define T2SH_FUSED_ROWS 0x8u /* t2sh_solve: one kernel per iteration for the row adjoint,
+                                gradient step, LLR, momentum and row forward of each 8-row
+                                LLR band (M = 1, K <= 4, block 8, nz in {48..192}); off by
+                                default: measured slower than the separate kernels        */
 
 typedef struct {
   int32_t ny, nz;          /* slice matrix (phase encodes y, z); both even, 2/3/5-smooth,
@@ -79,7 +83,7 @@ typedef struct {
   float step;              /* > 0: FISTA step mu; <= 0: the plan computes mu = 1/L with
                               L = max_n lambda_max Psi(n) * max_p lambda_max S(p)^H S(p) */
   int32_t precision;       /* T2SH_FP32 (T2SH_MIXED_BF16: reserved, T2SH_EUNSUPPORTED)   */
-  uint32_t flags;          /* T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64                */
+  uint32_t flags;          /* T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64 | T2SH_FUSED_ROWS */
 } t2sh_dims;
 
 typedef struct t2sh_plan_s* t2sh_plan_t;
@@ -178,6 +182,7 @@ t2sh_status t2sh_workspace_bytes(const t2sh_dims* dims, size_t* bytes);
  *   2 column pass       (DFT_y, Psi, IDFT_y or variants)  3 LLR prox / FISTA update
  *   4 (reserved: plan-time kernels run inside t2sh_plan, before timing can be enabled)
  *   5 projection of per-echo k-space
+ *   6 fused band kernel of t2sh_solve (row adjoint + gradient + LLR + momentum + row forward)
  * t2sh_timing_enable(plan, 1) clears the counters and starts recording; (plan, 0) stops.
  * t2sh_timing_read synchronises the stream and returns the launch count and the summed
  * event-to-event milliseconds of one class since the last enable.  Recording adds two

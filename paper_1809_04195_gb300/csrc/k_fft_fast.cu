@@ -18,13 +18,8 @@
 
 namespace t2sh {
 
-// odd row strides of the exchange layouts (bank-conflict-free half-warp access)
 template <int R1>
-struct Ex {
-  static constexpr int SF = (R1 % 2) ? R1 : R1 + 1;  // forward: [j < 16][r1 < R1]
-  static constexpr int SI = 17;                        // inverse: [j' < R1][r1 < 16]
-  static constexpr int LINE = (16 * SF > R1 * SI) ? 16 * SF : R1 * SI;
-};
+using Ex = ExLayout<R1>;
 
 // ------------------------------------------------------------------------------------
 // Row pass.  CTA = (slice, band of RB rows), 16 x 4 x RB threads, thread

@@ -92,88 +92,8 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
   __syncthreads();
 
   // 3. eigendecomposition and threshold weights, one thread per block
-  for (int blk = threadIdx.x; blk < nblk; blk += kThreads) {
-    ET ar[KC][KC], ai[KC][KC], vr[KC][KC], vi[KC][KC];
-    const float* gp = gram + blk * KC * KC;
-#pragma unroll
-    for (int k = 0; k < KC; ++k)
-#pragma unroll
-      for (int l = 0; l < KC; ++l) {
-        if (k == l) { ar[k][l] = gp[k * KC + k]; ai[k][l] = ET(0); }
-        else if (k < l) { ar[k][l] = gp[k * KC + l]; ai[k][l] = gp[l * KC + k]; }
-        else { ar[k][l] = gp[l * KC + k]; ai[k][l] = -gp[k * KC + l]; }
-      }
-    herm_jacobi<ET, KC>(ar, ai, vr, vi, 5);
-    // Five cyclic sweeps converge a 4 x 4 Hermitian matrix to working precision.
-    // Rotations accumulated in float32 drift V away from orthonormal, and FISTA's
-    // momentum amplifies the resulting error in W; so re-orthonormalise V (modified
-    // Gram-Schmidt) and take each eigenvalue as the Rayleigh quotient v^H G v on the
-    // original Gram matrix.
-#pragma unroll
-    for (int i = 0; i < KC; ++i) {
-#pragma unroll
-      for (int j = 0; j < i; ++j) {
-        ET pr = ET(0), pi = ET(0);  // v_j^H v_i
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-          pr += vr[k][j] * vr[k][i] + vi[k][j] * vi[k][i];
-          pi += vr[k][j] * vi[k][i] - vi[k][j] * vr[k][i];
-        }
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-          const ET nr = vr[k][i] - (pr * vr[k][j] - pi * vi[k][j]);
-          const ET ni = vi[k][i] - (pr * vi[k][j] + pi * vr[k][j]);
-          vr[k][i] = nr;
-          vi[k][i] = ni;
-        }
-      }
-      ET nn = ET(0);
-#pragma unroll
-      for (int k = 0; k < KC; ++k) nn += vr[k][i] * vr[k][i] + vi[k][i] * vi[k][i];
-      const ET inv = nn > ET(0) ? ET(1) / sqrt(nn) : ET(0);
-#pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        vr[k][i] *= inv;
-        vi[k][i] *= inv;
-      }
-    }
-    ET f[KC];
-#pragma unroll
-    for (int i = 0; i < KC; ++i) {
-      // lambda_i = v_i^H G v_i, G Hermitian from the stored upper triangle
-      ET lam = ET(0);
-#pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        ET gvr = ET(0), gvi = ET(0);  // (G v_i)_k
-#pragma unroll
-        for (int l = 0; l < KC; ++l) {
-          ET gr_, gi_;
-          if (k == l) { gr_ = gp[k * KC + k]; gi_ = ET(0); }
-          else if (k < l) { gr_ = gp[k * KC + l]; gi_ = gp[l * KC + k]; }
-          else { gr_ = gp[l * KC + k]; gi_ = -gp[k * KC + l]; }
-          gvr += gr_ * vr[l][i] - gi_ * vi[l][i];
-          gvi += gr_ * vi[l][i] + gi_ * vr[l][i];
-        }
-        lam += vr[k][i] * gvr + vi[k][i] * gvi;
-      }
-      const ET sig = sqrt(lam > ET(0) ? lam : ET(0));
-      f[i] = (sig > (ET)a.tau) ? ET(1) - (ET)a.tau / sig : ET(0);
-    }
-    float2* w = wm + (size_t)blk * KC * KC;
-#pragma unroll
-    for (int l = 0; l < KC; ++l)
-#pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        // W_lk = sum_i V_li f_i conj(V_ki)
-        ET wr = ET(0), wi = ET(0);
-#pragma unroll
-        for (int i = 0; i < KC; ++i) {
-          wr += f[i] * (vr[l][i] * vr[k][i] + vi[l][i] * vi[k][i]);
-          wi += f[i] * (vi[l][i] * vr[k][i] - vr[l][i] * vi[k][i]);
-        }
-        w[l * KC + k] = make_float2((float)wr, (float)wi);
-      }
-  }
+  for (int blk = threadIdx.x; blk < nblk; blk += kThreads)
+    svt_weights<ET, KC>(gram + blk * KC * KC, a.tau, wm + (size_t)blk * KC * KC);
   __syncthreads();
 
   // 4. X' = X W, then FISTA momentum; write back.  The optional convergence monitor sums

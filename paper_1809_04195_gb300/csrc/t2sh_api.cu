@@ -126,7 +126,8 @@ t2sh_status validate(const t2sh_dims* d) {
     set_err("precision %d not implemented", d->precision);
     return T2SH_EUNSUPPORTED;
   }
-  T2SH_REQ((d->flags & ~(T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64)) == 0, "unknown flag bits");
+  T2SH_REQ((d->flags & ~(T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64 | T2SH_FUSED_ROWS)) == 0,
+           "unknown flag bits");
   Geom g{};
   g.M = d->nmaps; g.K = d->nbasis; g.nz = d->nz;
   if (llr_smem_bytes(g, d->block) > 200 * 1024) {
@@ -170,12 +171,12 @@ struct t2sh_plan_s {
   float mu = 1.f;
   std::vector<void*> allocs;
   // kernel timing (t2sh_timing_*)
-  static constexpr int kClasses = 6;
+  static constexpr int kClasses = 7;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   size_t ev_next = 0;
-  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0};
+  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0, 0};
 
   template <typename T>
   t2sh_status alloc(T** p, size_t bytes) {
@@ -227,7 +228,7 @@ struct KTimer {
     }
   }
 };
-enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5 };
+enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5, KC_BAND = 6 };
 }  // namespace
 
 namespace {
@@ -482,13 +483,8 @@ t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* a
   T2SH_CK(cudaMemsetAsync(p->z, 0, vec, p->st));
   if (residual_out) T2SH_CK(cudaMemsetAsync(p->res, 0, sizeof(double) * 2 * (size_t)d.iters, p->st));
   double tk = 1.0;
+  const bool fused = (d.flags & T2SH_FUSED_ROWS) && band_fused_supported(p->g, d.block);
   for (int it = 0; it < d.iters; ++it) {
-    if (it == 0) {
-      T2SH_CK(cudaMemsetAsync(p->grad, 0, vec, p->st));  // z_0 = 0
-    } else {
-      s = normal_op(p, p->z, p->grad);
-      if (s != T2SH_OK) return s;
-    }
     const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * tk * tk));
     FistaArgs a{};
     a.mu = p->mu;
@@ -498,8 +494,28 @@ t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* a
     a.sz = p->shifts[2 * it + 1];
     a.b = d.block;
     a.eig64 = (d.flags & T2SH_EIG_FP64) ? 1 : 0;
+    a.skip_adj = (it == 0);
+    a.skip_fwd = (it == d.iters - 1);
     a.res = residual_out ? p->res + 2 * it : nullptr;
-    { KTimer k(p, KC_LLR); T2SH_CK(launch_llr(p->g, a, p->x, p->z, p->grad, p->aty, p->st)); }
+    if (fused) {
+      // column pass of the normal operator, then the band kernel: A^H A z, gradient,
+      // LLR, momentum and DFT_z(S z_{k+1}) for the next iteration (z_0 = 0: no A^H A z_0)
+      if (it > 0) {
+        KTimer k(p, KC_COL);
+        T2SH_CK(launch_col(p->g, COL_NORMAL, p->py, p->tw_y, p->psi, p->phi, p->mask, p->t, p->t, p->st));
+      }
+      KTimer k(p, KC_BAND);
+      T2SH_CK(launch_band_fused(p->g, a, p->tw_z, p->maps, p->t, p->x, p->z, p->aty, p->st));
+    } else {
+      if (it == 0) {
+        T2SH_CK(cudaMemsetAsync(p->grad, 0, vec, p->st));  // z_0 = 0
+      } else {
+        s = normal_op(p, p->z, p->grad);
+        if (s != T2SH_OK) return s;
+      }
+      KTimer k(p, KC_LLR);
+      T2SH_CK(launch_llr(p->g, a, p->x, p->z, p->grad, p->aty, p->st));
+    }
     tk = tn;
   }
   T2SH_CK(cudaMemcpyAsync(alpha_out, p->x, vec, p->host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,

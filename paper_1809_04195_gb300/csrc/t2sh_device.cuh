@@ -369,6 +369,103 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ---------------------------------------------------------------------------------
+// Singular-value soft threshold of one LLR block through its K x K Gram matrix:
+// G = X^H X = V diag(lambda) V^H, sigma_i = sqrt(lambda_i), and the block's threshold
+// weights W = V diag(max(1 - tau / sigma_i, 0)) V^H, so that X W = U max(Sigma - tau, 0) V^H
+// (X V = U Sigma).  gram holds G as KC*KC floats: real part at [k][l] for k <= l, imaginary
+// part of G_kl at [l][k] for l > k.  W_lk is written to w[l * KC + k].
+// ---------------------------------------------------------------------------------
+template <typename ET, int KC>
+__device__ __forceinline__ void svt_weights(const float* gp, float tau, float2* w) {
+  ET ar[KC][KC], ai[KC][KC], vr[KC][KC], vi[KC][KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k)
+#pragma unroll
+    for (int l = 0; l < KC; ++l) {
+      if (k == l) { ar[k][l] = gp[k * KC + k]; ai[k][l] = ET(0); }
+      else if (k < l) { ar[k][l] = gp[k * KC + l]; ai[k][l] = gp[l * KC + k]; }
+      else { ar[k][l] = gp[l * KC + k]; ai[k][l] = -gp[k * KC + l]; }
+    }
+  // Five cyclic sweeps converge a 4 x 4 Hermitian matrix to working precision.
+  herm_jacobi<ET, KC>(ar, ai, vr, vi, 5);
+  // Rotations accumulated in float32 drift V away from orthonormal, and FISTA's
+  // momentum amplifies the resulting error in W; so re-orthonormalise V (modified
+  // Gram-Schmidt) and take each eigenvalue as the Rayleigh quotient v^H G v on the
+  // original Gram matrix.
+#pragma unroll
+  for (int i = 0; i < KC; ++i) {
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      ET pr = ET(0), pi = ET(0);  // v_j^H v_i
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        pr += vr[k][j] * vr[k][i] + vi[k][j] * vi[k][i];
+        pi += vr[k][j] * vi[k][i] - vi[k][j] * vr[k][i];
+      }
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const ET nr = vr[k][i] - (pr * vr[k][j] - pi * vi[k][j]);
+        const ET ni = vi[k][i] - (pr * vi[k][j] + pi * vr[k][j]);
+        vr[k][i] = nr;
+        vi[k][i] = ni;
+      }
+    }
+    ET nn = ET(0);
+#pragma unroll
+    for (int k = 0; k < KC; ++k) nn += vr[k][i] * vr[k][i] + vi[k][i] * vi[k][i];
+    const ET inv = nn > ET(0) ? ET(1) / sqrt(nn) : ET(0);
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      vr[k][i] *= inv;
+      vi[k][i] *= inv;
+    }
+  }
+  ET f[KC];
+#pragma unroll
+  for (int i = 0; i < KC; ++i) {
+    ET lam = ET(0);
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      ET gvr = ET(0), gvi = ET(0);  // (G v_i)_k
+#pragma unroll
+      for (int l = 0; l < KC; ++l) {
+        ET gr_, gi_;
+        if (k == l) { gr_ = gp[k * KC + k]; gi_ = ET(0); }
+        else if (k < l) { gr_ = gp[k * KC + l]; gi_ = gp[l * KC + k]; }
+        else { gr_ = gp[l * KC + k]; gi_ = -gp[k * KC + l]; }
+        gvr += gr_ * vr[l][i] - gi_ * vi[l][i];
+        gvi += gr_ * vi[l][i] + gi_ * vr[l][i];
+      }
+      lam += vr[k][i] * gvr + vi[k][i] * gvi;
+    }
+    const ET sig = sqrt(lam > ET(0) ? lam : ET(0));
+    f[i] = (sig > (ET)tau) ? ET(1) - (ET)tau / sig : ET(0);
+  }
+#pragma unroll
+  for (int l = 0; l < KC; ++l)
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      // W_lk = sum_i V_li f_i conj(V_ki)
+      ET wr = ET(0), wi = ET(0);
+#pragma unroll
+      for (int i = 0; i < KC; ++i) {
+        wr += f[i] * (vr[l][i] * vr[k][i] + vi[l][i] * vi[k][i]);
+        wi += f[i] * (vi[l][i] * vr[k][i] - vr[l][i] * vi[k][i]);
+      }
+      w[l * KC + k] = make_float2((float)wr, (float)wi);
+    }
+}
+
+// Exchange layouts of the two-stage line transforms (N = 16 R1): odd row strides keep
+// half-warp accesses free of bank conflicts.
+template <int R1>
+struct ExLayout {
+  static constexpr int SF = (R1 % 2) ? R1 : R1 + 1;  // forward: [j < 16][r1 < R1]
+  static constexpr int SI = 17;                        // inverse: [j' < R1][r1 < 16]
+  static constexpr int LINE = (16 * SF > R1 * SI) ? 16 * SF : R1 * SI;
+};
+
 // sign (-1)^(a) as float
 __device__ __forceinline__ float parity_sign(int a) { return (a & 1) ? -1.0f : 1.0f; }
 

@@ -55,6 +55,8 @@ struct FistaArgs {
   int sy, sz;    // LLR shift of this iteration
   int b;         // block edge
   int eig64;     // 1: eigendecomposition in float64, 0: float32
+  int skip_adj;  // fused band kernel: z_k = 0, so A^H A z_k = 0 (first iteration)
+  int skip_fwd;  // fused band kernel: no next iteration, skip DFT_z(S z_{k+1})
   double* res;   // nullable: accumulates {sum |x_{k+1} - x_k|^2, sum |x_{k+1}|^2}
 };
 
@@ -77,6 +79,11 @@ cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, 
 cudaError_t launch_row_fast(const Geom& g, RowMode mode, const float2* tw_z, const float2* maps, const float2* x,
                             float2* t, float2* out, cudaStream_t st);
 cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
+
+// fused row work of one FISTA iteration (k_fused.cu)
+bool band_fused_supported(const Geom& g, int block);
+cudaError_t launch_band_fused(const Geom& g, const FistaArgs& a, const float2* tw_z, const float2* maps, float2* t,
+                              float2* x, float2* z, const float2* aty, cudaStream_t st);
 
 int row_rows_per_cta(const Geom& g);
 int col_cols_per_cta(const Geom& g);

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "t2sh.h")
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, EBUSY = range(7)
 FP32, MIXED_BF16 = 0, 1
 KSPACE_TE, KSPACE_PROJ = 0, 1
-NO_SHIFT, HOST_IO, EIG_FP64 = 0x1, 0x2, 0x4
+NO_SHIFT, HOST_IO, EIG_FP64, FUSED_ROWS = 0x1, 0x2, 0x4, 0x8
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "ETIMEOUT", 6: "EBUSY"}
 
 
@@ -240,7 +240,7 @@ class Plan:
         return (out, res) if residual else out
 
     # -- kernel timing ----------------------------------------------------------------
-    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project"}
+    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band"}
 
     def timing(self, enable: bool):
         _check(lib().t2sh_timing_enable(self._h, 1 if enable else 0))

@@ -58,7 +58,7 @@ def test_workspace_bytes_formula(lib):
     (dict(nechoes=3), t2sh.EINVAL),      # T < K
     (dict(precision=t2sh.MIXED_BF16), t2sh.EUNSUPPORTED),
     (dict(flags=0x80), t2sh.EINVAL),
-    (dict(flags=0x8), t2sh.EINVAL),
+    (dict(flags=0x10), t2sh.EINVAL),
 ])
 def test_invalid_dims_rejected(lib, kw, status):
     base = dict(ny=64, nz=48, ncoils=8, nechoes=32, nbasis=4, nslices=1, block=8, iters=10)

@@ -168,8 +168,8 @@ def test_llr_prox_limits(T):
         assert float(a.abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("eig64", [False, True])
-def test_solve_single_slice_64x48(T, eig64):
+@pytest.mark.parametrize("eig64,fused", [(False, False), (True, False), (False, True), (True, True)])
+def test_solve_single_slice_64x48(T, eig64, fused):
     """The 64 x 48, C=8, T=32, K=4, 10 %/echo, lambda=0.01, 50-iteration single slice,
     per-echo (TE-form) input, against the oracle's FISTA; float32 and float64 LLR
     eigendecompositions."""
@@ -178,8 +178,9 @@ def test_solve_single_slice_64x48(T, eig64):
     phi, maps = r32(phi, maps)
     ys = y.astype(np.complex64).astype(np.complex128)
     ref = O.fista(ys, "te", maps, mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
+    flags = (T.EIG_FP64 if eig64 else 0) | (T.FUSED_ROWS if fused else 0)
     with make_plan(T, phi, mask, maps[None], block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed,
-                   flags=T.EIG_FP64 if eig64 else 0) as p:
+                   flags=flags) as p:
         got, res = p.solve(c64(y[None]), T.KSPACE_TE, residual=True)
         got = host(got)[0]
     e = nrmse(got, ref)
@@ -249,6 +250,10 @@ def test_solve_knee_slices_projected(T):
     phi, maps = r32(phi, maps)
     with make_plan(T, phi, mask, maps, block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed) as p:
         got = host(p.solve(c64(ytil), T.KSPACE_PROJ))
+    with make_plan(T, phi, mask, maps, block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed,
+                   flags=T.FUSED_ROWS) as p:
+        got_fused = host(p.solve(c64(ytil), T.KSPACE_PROJ))
+    assert nrmse(got_fused, got) < 1e-5
     ys = ytil.astype(np.complex64).astype(np.complex128)
     for i in (0, 3):
         ref = O.fista(ys[i], "proj", maps[i], mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
