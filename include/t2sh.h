@@ -160,6 +160,47 @@ t2sh_status t2sh_llr_prox(t2sh_plan_t plan, void* x, float tau, int32_t sy, int3
 t2sh_status t2sh_solve(t2sh_plan_t plan, const void* kspace, int32_t kform, void* alpha_out,
                        double* residual_out);
 
+/*
+ * Resumable solve, for schedulers that interleave several scans (t2sh_solve is
+ * t2sh_solve_begin + t2sh_solve_iterate(dims.iters) + t2sh_solve_end):
+ *   t2sh_solve_begin    forms A^H y from the k-space (as t2sh_solve) and resets the FISTA
+ *                       state: x = z = 0, t = 1, iteration counter 0; the convergence
+ *                       monitor is recorded.
+ *   t2sh_solve_iterate  runs the next min(n, dims.iters - done) iterations; *done (nullable)
+ *                       receives the number of iterations completed so far.  The state
+ *                       (x, z, t_k, counter) stays on the device between calls.
+ *   t2sh_solve_end      copies x into alpha_out (host pointer with T2SH_HOST_IO, then the
+ *                       call synchronises) and, if residual_out is non-NULL, the monitor of
+ *                       the completed iterations (synchronises).
+ * Errors: EINVAL if begin was not called.
+ */
+t2sh_status t2sh_solve_begin(t2sh_plan_t plan, const void* kspace, int32_t kform);
+t2sh_status t2sh_solve_iterate(t2sh_plan_t plan, int32_t n, int32_t* done);
+t2sh_status t2sh_solve_end(t2sh_plan_t plan, void* alpha_out, double* residual_out);
+
+/*
+ * t2sh_solve_batch -- solve n plans at once (scans of different sizes and coil counts:
+ * the batched multi-scan form).  Each plan runs on a stream forked from `stream`; all
+ * iterations of all plans are captured into one CUDA graph, which is launched once, so
+ * the scans' kernels overlap on the GPU.  kspace[i] / kform[i] / alpha_out[i] as for
+ * t2sh_solve (device pointers; plans with T2SH_HOST_IO are rejected).  A plan may
+ * appear once.  Synchronous: returns when every alpha_out is written.
+ */
+t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* kspace, const int32_t* kform,
+                             void* const* alpha_out, void* stream);
+
+/*
+ * t2sh_autotune -- choose, for the plan's problem shape, the column-pass tile width
+ * (8 or 4 columns) and separate versus fused row kernels, by timing probe_iters
+ * iterations (default 3 when <= 0) of each candidate on the plan's buffers; the choice
+ * is remembered per shape (and appended to the file named by the environment variable
+ * T2SH_TUNE_CACHE, read back by later processes).  With probe_iters >= 0 a shape that is
+ * already known is not timed again; probe_iters < 0 forces a new measurement.  Clobbers
+ * the plan's FISTA state: call it before t2sh_solve_begin.  Synchronises the stream.
+ * colw_out / fused_out (nullable) receive the choice.
+ */
+t2sh_status t2sh_autotune(t2sh_plan_t plan, int32_t probe_iters, int32_t* colw_out, int32_t* fused_out);
+
 /* The step mu the plan uses (host float). */
 t2sh_status t2sh_get_step(t2sh_plan_t plan, float* step);
 

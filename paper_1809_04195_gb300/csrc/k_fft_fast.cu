@@ -392,8 +392,8 @@ static cudaError_t col_fast_go(const Geom& g, const float2* tw, const float* psi
   return cudaGetLastError();
 }
 
-cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
-  constexpr int W = kColW;
+template <int W>
+static cudaError_t col_fast_w(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
   if (g.K > 4 || g.nz % W != 0) return cudaErrorNotSupported;
   switch (g.ny) {
     case 48: return col_fast_go<48, W>(g, tw_y, psi, t, st);
@@ -406,6 +406,10 @@ cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const floa
     case 256: return col_fast_go<256, W>(g, tw_y, psi, t, st);
     default: return cudaErrorNotSupported;
   }
+}
+
+cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
+  return g.colw == 4 ? col_fast_w<4>(g, tw_y, psi, t, st) : col_fast_w<kColW>(g, tw_y, psi, t, st);
 }
 
 }  // namespace t2sh

@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -170,6 +173,12 @@ struct t2sh_plan_s {
   std::vector<int32_t> shifts;
   float mu = 1.f;
   std::vector<void*> allocs;
+  // resumable FISTA state (t2sh_solve_begin / _iterate / _end)
+  bool begun = false;
+  int iter_done = 0;
+  double tk = 1.0;
+  bool record_res = false;
+  bool fused_rows = false;  // tunable: fused band kernel for the row work
   // kernel timing (t2sh_timing_*)
   static constexpr int kClasses = 7;
   bool timing = false;
@@ -305,6 +314,8 @@ t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* ma
   g.ny = d.ny; g.nz = d.nz; g.P = d.nbasis * (d.nbasis + 1) / 2;
   g.gsign = (((d.ny / 2) + (d.nz / 2)) & 1) ? -1.f : 1.f;
   g.inv_sqrt_n = (float)(1.0 / std::sqrt((double)d.ny * d.nz));
+  g.colw = 8;
+  p->fused_rows = (d.flags & T2SH_FUSED_ROWS) != 0;
   if (!make_fft_plan(d.ny, p->py) || !make_fft_plan(d.nz, p->pz)) {
     delete p;
     set_err("no radix plan for ny=%d nz=%d", d.ny, d.nz);
@@ -455,8 +466,13 @@ t2sh_status t2sh_llr_prox(t2sh_plan_t p, void* x, float tau, int32_t sy, int32_t
   return T2SH_OK;
 }
 
-t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* alpha_out, double* residual_out) {
-  T2SH_REQ(p && kspace && alpha_out, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// A^H y from the k-space (staged through the plan with T2SH_HOST_IO) and a fresh FISTA state.
+t2sh_status begin_impl(t2sh_plan_t p, const void* kspace, int32_t kform, bool record_res) {
+  T2SH_REQ(p && kspace, "NULL argument");
   T2SH_REQ(kform == T2SH_KSPACE_TE || kform == T2SH_KSPACE_PROJ, "bad kform %d", kform);
   const t2sh_dims& d = p->d;
   const size_t vec = footprint(d).vec;
@@ -481,50 +497,79 @@ t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* a
   if (s != T2SH_OK) return s;
   T2SH_CK(cudaMemsetAsync(p->x, 0, vec, p->st));
   T2SH_CK(cudaMemsetAsync(p->z, 0, vec, p->st));
-  if (residual_out) T2SH_CK(cudaMemsetAsync(p->res, 0, sizeof(double) * 2 * (size_t)d.iters, p->st));
-  double tk = 1.0;
-  const bool fused = (d.flags & T2SH_FUSED_ROWS) && band_fused_supported(p->g, d.block);
-  for (int it = 0; it < d.iters; ++it) {
-    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * tk * tk));
-    FistaArgs a{};
-    a.mu = p->mu;
-    a.tau = p->mu * d.lambda;
-    a.beta = (float)((tk - 1.0) / tn);
-    a.sy = p->shifts[2 * it];
-    a.sz = p->shifts[2 * it + 1];
-    a.b = d.block;
-    a.eig64 = (d.flags & T2SH_EIG_FP64) ? 1 : 0;
-    a.skip_adj = (it == 0);
-    a.skip_fwd = (it == d.iters - 1);
-    a.res = residual_out ? p->res + 2 * it : nullptr;
-    if (fused) {
-      // column pass of the normal operator, then the band kernel: A^H A z, gradient,
-      // LLR, momentum and DFT_z(S z_{k+1}) for the next iteration (z_0 = 0: no A^H A z_0)
-      if (it > 0) {
-        KTimer k(p, KC_COL);
-        T2SH_CK(launch_col(p->g, COL_NORMAL, p->py, p->tw_y, p->psi, p->phi, p->mask, p->t, p->t, p->st));
-      }
-      KTimer k(p, KC_BAND);
-      T2SH_CK(launch_band_fused(p->g, a, p->tw_z, p->maps, p->t, p->x, p->z, p->aty, p->st));
-    } else {
-      if (it == 0) {
-        T2SH_CK(cudaMemsetAsync(p->grad, 0, vec, p->st));  // z_0 = 0
-      } else {
-        s = normal_op(p, p->z, p->grad);
-        if (s != T2SH_OK) return s;
-      }
-      KTimer k(p, KC_LLR);
-      T2SH_CK(launch_llr(p->g, a, p->x, p->z, p->grad, p->aty, p->st));
+  if (record_res && d.iters > 0) T2SH_CK(cudaMemsetAsync(p->res, 0, sizeof(double) * 2 * (size_t)d.iters, p->st));
+  p->begun = true;
+  p->iter_done = 0;
+  p->tk = 1.0;
+  p->record_res = record_res;
+  return T2SH_OK;
+}
+
+// One FISTA iteration (index p->iter_done) of Eq. 5.
+t2sh_status iteration(t2sh_plan_t p) {
+  const t2sh_dims& d = p->d;
+  const size_t vec = footprint(d).vec;
+  const int it = p->iter_done;
+  const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * p->tk * p->tk));
+  FistaArgs a{};
+  a.mu = p->mu;
+  a.tau = p->mu * d.lambda;
+  a.beta = (float)((p->tk - 1.0) / tn);
+  a.sy = p->shifts[2 * it];
+  a.sz = p->shifts[2 * it + 1];
+  a.b = d.block;
+  a.eig64 = (d.flags & T2SH_EIG_FP64) ? 1 : 0;
+  a.skip_adj = (it == 0);
+  a.skip_fwd = (it == d.iters - 1);
+  a.res = p->record_res ? p->res + 2 * it : nullptr;
+  if (p->fused_rows && band_fused_supported(p->g, d.block)) {
+    // column pass of the normal operator, then the band kernel: A^H A z, gradient,
+    // LLR, momentum and DFT_z(S z_{k+1}) for the next iteration (z_0 = 0: no A^H A z_0)
+    if (it > 0) {
+      KTimer k(p, KC_COL);
+      T2SH_CK(launch_col(p->g, COL_NORMAL, p->py, p->tw_y, p->psi, p->phi, p->mask, p->t, p->t, p->st));
     }
-    tk = tn;
+    KTimer k(p, KC_BAND);
+    T2SH_CK(launch_band_fused(p->g, a, p->tw_z, p->maps, p->t, p->x, p->z, p->aty, p->st));
+  } else {
+    if (it == 0) {
+      T2SH_CK(cudaMemsetAsync(p->grad, 0, vec, p->st));  // z_0 = 0
+    } else {
+      t2sh_status s = normal_op(p, p->z, p->grad);
+      if (s != T2SH_OK) return s;
+    }
+    KTimer k(p, KC_LLR);
+    T2SH_CK(launch_llr(p->g, a, p->x, p->z, p->grad, p->aty, p->st));
   }
+  p->tk = tn;
+  p->iter_done = it + 1;
+  return T2SH_OK;
+}
+
+t2sh_status iterate_impl(t2sh_plan_t p, int n) {
+  T2SH_REQ(p, "NULL plan");
+  T2SH_REQ(p->begun, "t2sh_solve_begin has not been called on this plan");
+  T2SH_REQ(n >= 0, "n must be >= 0");
+  for (int i = 0; i < n && p->iter_done < p->d.iters; ++i) {
+    t2sh_status s = iteration(p);
+    if (s != T2SH_OK) return s;
+  }
+  return T2SH_OK;
+}
+
+t2sh_status end_impl(t2sh_plan_t p, void* alpha_out, double* residual_out) {
+  T2SH_REQ(p && alpha_out, "NULL argument");
+  T2SH_REQ(p->begun, "t2sh_solve_begin has not been called on this plan");
+  const t2sh_dims& d = p->d;
+  const size_t vec = footprint(d).vec;
   T2SH_CK(cudaMemcpyAsync(alpha_out, p->x, vec, p->host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                           p->st));
-  if (residual_out && d.iters > 0) {
-    std::vector<double> r(2 * (size_t)d.iters);
+  if (residual_out && p->iter_done > 0) {
+    T2SH_REQ(p->record_res, "the monitor was not recorded for this solve");
+    std::vector<double> r(2 * (size_t)p->iter_done);
     T2SH_CK(cudaMemcpyAsync(r.data(), p->res, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, p->st));
     T2SH_CK(cudaStreamSynchronize(p->st));
-    for (int it = 0; it < d.iters; ++it)
+    for (int it = 0; it < p->iter_done; ++it)
       residual_out[it] = r[2 * it + 1] > 0.0 ? std::sqrt(r[2 * it] / r[2 * it + 1]) : 0.0;
   } else if (p->host_io) {
     T2SH_CK(cudaStreamSynchronize(p->st));
@@ -532,4 +577,242 @@ t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* a
   return T2SH_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* alpha_out, double* residual_out) {
+  T2SH_REQ(p && kspace && alpha_out, "NULL argument");
+  t2sh_status s = begin_impl(p, kspace, kform, residual_out != nullptr);
+  if (s == T2SH_OK) s = iterate_impl(p, p->d.iters);
+  if (s == T2SH_OK) s = end_impl(p, alpha_out, residual_out);
+  return s;
+}
+
+t2sh_status t2sh_solve_begin(t2sh_plan_t p, const void* kspace, int32_t kform) {
+  return begin_impl(p, kspace, kform, true);
+}
+
+t2sh_status t2sh_solve_iterate(t2sh_plan_t p, int32_t n, int32_t* done) {
+  t2sh_status s = iterate_impl(p, n);
+  if (s == T2SH_OK && done) *done = p->iter_done;
+  return s;
+}
+
+t2sh_status t2sh_solve_end(t2sh_plan_t p, void* alpha_out, double* residual_out) {
+  return end_impl(p, alpha_out, residual_out);
+}
+
+// ---------------------------------------------------------------------------------
+// Batched solve: several plans (scans of different sizes) on forked streams, every
+// iteration of every plan captured into one CUDA graph and launched once.
+// ---------------------------------------------------------------------------------
+t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* kspace, const int32_t* kform,
+                             void* const* alpha_out, void* stream) {
+  T2SH_REQ(plans && kspace && kform && alpha_out && n >= 1 && n <= 64, "bad batch arguments");
+  for (int i = 0; i < n; ++i) {
+    T2SH_REQ(plans[i] && kspace[i] && alpha_out[i], "NULL entry %d in the batch", i);
+    T2SH_REQ(!plans[i]->host_io, "batched solves take device pointers (plan %d has T2SH_HOST_IO)", i);
+    for (int j = 0; j < i; ++j) T2SH_REQ(plans[i] != plans[j], "plan %d appears twice in the batch", i);
+  }
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  std::vector<cudaStream_t> fs(n, nullptr);
+  std::vector<cudaStream_t> saved(n);
+  std::vector<bool> timing(n);
+  std::vector<cudaEvent_t> ev(n + 2, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  t2sh_status st = T2SH_OK;
+  cudaStream_t origin = nullptr;
+#define B_CK(call)                                                                   \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_err("%s failed: %s", #call, cudaGetErrorString(e_));                       \
+      st = T2SH_ECUDA;                                                               \
+      goto done;                                                                     \
+    }                                                                                \
+  } while (0)
+  for (auto& e : ev) B_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  B_CK(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+  for (int i = 0; i < n; ++i) B_CK(cudaStreamCreateWithFlags(&fs[i], cudaStreamNonBlocking));
+  // fork from the caller's stream, begin every solve (A^H y) on its own stream
+  B_CK(cudaEventRecord(ev[n], cs));
+  for (int i = 0; i < n; ++i) {
+    saved[i] = plans[i]->st;
+    timing[i] = plans[i]->timing;
+    plans[i]->st = fs[i];
+    plans[i]->timing = false;
+    B_CK(cudaStreamWaitEvent(fs[i], ev[n], 0));
+    st = begin_impl(plans[i], kspace[i], kform[i], false);
+    if (st != T2SH_OK) goto done;
+    B_CK(cudaEventRecord(ev[i], fs[i]));
+    B_CK(cudaStreamWaitEvent(origin, ev[i], 0));
+  }
+  // capture all iterations of all plans
+  B_CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed));
+  B_CK(cudaEventRecord(ev[n + 1], origin));
+  for (int i = 0; i < n; ++i) {
+    B_CK(cudaStreamWaitEvent(fs[i], ev[n + 1], 0));
+    st = iterate_impl(plans[i], plans[i]->d.iters);
+    if (st != T2SH_OK) {
+      cudaStreamEndCapture(origin, &graph);
+      goto done;
+    }
+    B_CK(cudaEventRecord(ev[i], fs[i]));
+    B_CK(cudaStreamWaitEvent(origin, ev[i], 0));
+  }
+  B_CK(cudaStreamEndCapture(origin, &graph));
+  B_CK(cudaGraphInstantiate(&exec, graph, 0));
+  B_CK(cudaGraphLaunch(exec, origin));
+  B_CK(cudaEventRecord(ev[n + 1], origin));
+  for (int i = 0; i < n; ++i) {
+    B_CK(cudaStreamWaitEvent(fs[i], ev[n + 1], 0));
+    st = end_impl(plans[i], alpha_out[i], nullptr);
+    if (st != T2SH_OK) goto done;
+    B_CK(cudaEventRecord(ev[i], fs[i]));
+    B_CK(cudaStreamWaitEvent(cs, ev[i], 0));
+  }
+  B_CK(cudaStreamSynchronize(cs));
+done:
+#undef B_CK
+  for (int i = 0; i < n; ++i)
+    if (fs[i]) {
+      cudaStreamSynchronize(fs[i]);
+      plans[i]->st = saved[i];
+      plans[i]->timing = timing[i];
+    }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (auto& f : fs)
+    if (f) cudaStreamDestroy(f);
+  if (origin) cudaStreamDestroy(origin);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return st;
+}
+
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Autotuner: per problem shape, time the column-pass tile width (8 or 4 columns) and
+// the separate or fused row kernels on the plan's own buffers; cache the choice in
+// memory and, when T2SH_TUNE_CACHE names a file, in that file (one line per shape).
+// ---------------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;  // shape -> (colw, fused)
+bool g_tune_loaded = false;
+
+std::string tune_key(const t2sh_dims& d) {
+  char b[128];
+  snprintf(b, sizeof(b), "%d %d %d %d %d %d", d.ny, d.nz, d.ncoils, d.nbasis, d.nmaps, d.block);
+  return b;
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = std::getenv("T2SH_TUNE_CACHE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  int a[8];
+  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6], &a[7]) == 8) {
+    char b[128];
+    snprintf(b, sizeof(b), "%d %d %d %d %d %d", a[0], a[1], a[2], a[3], a[4], a[5]);
+    g_tune[b] = {a[6], a[7]};
+  }
+  std::fclose(fp);
+}
+
+void tune_store(const std::string& key, int colw, int fused) {
+  const char* f = std::getenv("T2SH_TUNE_CACHE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d %d\n", key.c_str(), colw, fused);
+  std::fclose(fp);
+}
+}  // namespace
+
+extern "C" t2sh_status t2sh_autotune(t2sh_plan_t p, int32_t probe_iters, int32_t* colw_out, int32_t* fused_out) {
+  T2SH_REQ(p, "NULL plan");
+  T2SH_REQ(!p->begun || p->iter_done == p->d.iters, "autotune must not interrupt a solve in progress");
+  const t2sh_dims& d = p->d;
+  const std::string key = tune_key(d);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && probe_iters >= 0) {
+      p->g.colw = it->second.first;
+      p->fused_rows = it->second.second != 0;
+      if (colw_out) *colw_out = p->g.colw;
+      if (fused_out) *fused_out = p->fused_rows ? 1 : 0;
+      return T2SH_OK;
+    }
+  }
+  const int probe = probe_iters > 0 ? probe_iters : 3;
+  const int iters_keep = d.iters;
+  T2SH_REQ(iters_keep >= 2, "autotune needs a plan with at least 2 iterations");
+  const size_t vec = footprint(d).vec;
+  T2SH_CK(cudaMemsetAsync(p->x, 0, vec, p->st));
+  T2SH_CK(cudaMemsetAsync(p->z, 0, vec, p->st));
+  T2SH_CK(cudaMemsetAsync(p->aty, 0, vec, p->st));
+  T2SH_CK(cudaMemsetAsync(p->t, 0, footprint(d).t, p->st));
+  cudaEvent_t e0, e1;
+  T2SH_CK(cudaEventCreate(&e0));
+  T2SH_CK(cudaEventCreate(&e1));
+  const bool timing = p->timing;
+  p->timing = false;
+  float best = 1e30f;
+  int bw = 8, bf = 0;
+  t2sh_status st = T2SH_OK;
+  for (int colw : {8, 4}) {
+    for (int fused = 0; fused <= (band_fused_supported(p->g, d.block) ? 1 : 0); ++fused) {
+      p->g.colw = colw;
+      p->fused_rows = fused != 0;
+      p->begun = true;
+      p->record_res = false;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && st == T2SH_OK; ++rep) {  // first repetition warms up
+        p->iter_done = 1;
+        p->tk = 1.0;
+        if (cudaEventRecord(e0, p->st) != cudaSuccess) st = T2SH_ECUDA;
+        for (int i = 0; i < probe && st == T2SH_OK; ++i) {
+          p->iter_done = 1 + (i % (iters_keep - 1));
+          st = iteration(p);
+        }
+        if (st == T2SH_OK && cudaEventRecord(e1, p->st) != cudaSuccess) st = T2SH_ECUDA;
+        if (st == T2SH_OK && cudaEventSynchronize(e1) != cudaSuccess) st = T2SH_ECUDA;
+        if (st == T2SH_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = T2SH_ECUDA;
+      }
+      if (st != T2SH_OK) break;
+      if (ms < best) {
+        best = ms;
+        bw = colw;
+        bf = fused;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->timing = timing;
+  p->begun = false;
+  p->iter_done = 0;
+  if (st != T2SH_OK) {
+    if (g_err.empty()) set_err("autotune: a CUDA call failed");
+    return st;
+  }
+  p->g.colw = bw;
+  p->fused_rows = bf != 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {bw, bf};
+    tune_store(key, bw, bf);
+  }
+  if (colw_out) *colw_out = bw;
+  if (fused_out) *fused_out = bf;
+  return T2SH_OK;
+}

@@ -32,6 +32,7 @@ struct Geom {
   int P;               // K (K + 1) / 2: stored entries of Psi(n)
   float gsign;         // (-1)^(ny/2 + nz/2): global sign of the centred DFT
   float inv_sqrt_n;    // 1 / sqrt(ny nz)
+  int colw;            // columns per tile of the size-specialised column pass (4 or 8)
 };
 
 // Column-pass (ky direction) modes.

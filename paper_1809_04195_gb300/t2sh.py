@@ -66,6 +66,12 @@ def lib() -> ctypes.CDLL:
             "t2sh_shifts": [_u64, _i32, _i32, ctypes.POINTER(_i32)],
             "t2sh_workspace_bytes": [ctypes.POINTER(Dims), ctypes.POINTER(ctypes.c_size_t)],
             "t2sh_timing_enable": [_vp, _i32],
+            "t2sh_solve_begin": [_vp, _vp, _i32],
+            "t2sh_solve_iterate": [_vp, _i32, ctypes.POINTER(_i32)],
+            "t2sh_solve_end": [_vp, _vp, ctypes.POINTER(ctypes.c_double)],
+            "t2sh_solve_batch": [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i32),
+                                 ctypes.POINTER(_vp), _vp],
+            "t2sh_autotune": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
             "t2sh_timing_read": [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
@@ -156,6 +162,22 @@ def noalloc_scratch_bytes() -> int:
     return int(lib().t2sh_noalloc_scratch_bytes())
 
 
+def solve_batch(plans, kspaces, kforms=None, outs=None, stream=None):
+    """Solve several plans (scans of different shapes) at once: forked streams, every
+    iteration captured into one CUDA graph (t2sh_solve_batch).  Returns the outputs."""
+    import torch
+    n = len(plans)
+    kforms = [KSPACE_PROJ] * n if kforms is None else list(kforms)
+    outs = [p._empty(p.vec_shape) for p in plans] if outs is None else list(outs)
+    hp = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    kp = (ctypes.c_void_p * n)(*[p._dev(k, p._kshape(f)).value for p, k, f in zip(plans, kspaces, kforms)])
+    op = (ctypes.c_void_p * n)(*[p._dev(o, p.vec_shape).value for p, o in zip(plans, outs)])
+    kf = (ctypes.c_int32 * n)(*kforms)
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().t2sh_solve_batch(hp, n, kp, kf, op, ctypes.c_void_p(st.cuda_stream)))
+    return outs
+
+
 class Plan:
     """One batch of slices sharing a basis, a sampling pattern and dimensions.
 
@@ -238,6 +260,38 @@ class Plan:
             rp = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         _check(lib().t2sh_solve(self._h, kp, kform, op, rp))
         return (out, res) if residual else out
+
+    # -- resumable solve (schedulers interleaving scans) --------------------------------
+    def solve_begin(self, kspace, kform=KSPACE_PROJ):
+        import torch
+        self._kin = kspace  # keep the caller's array alive until the solve ends
+        kp = _ptr(kspace, torch.complex64, self._kshape(kform), self.host_io)
+        _check(lib().t2sh_solve_begin(self._h, kp, kform))
+
+    def solve_iterate(self, n: int) -> int:
+        done = ctypes.c_int32(0)
+        _check(lib().t2sh_solve_iterate(self._h, int(n), ctypes.byref(done)))
+        return int(done.value)
+
+    def solve_end(self, out=None, residual: bool = False):
+        import torch
+        if self.host_io:
+            out = np.empty(self.vec_shape, np.complex64) if out is None else out
+            op = _ptr(out, torch.complex64, self.vec_shape, True)
+        else:
+            out = self._empty(self.vec_shape) if out is None else out
+            op = self._dev(out, self.vec_shape)
+        res = np.zeros(max(self.dims.iters, 0), np.float64) if residual else None
+        rp = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if residual else None
+        _check(lib().t2sh_solve_end(self._h, op, rp))
+        self._kin = None
+        return (out, res) if residual else out
+
+    def autotune(self, probe_iters: int = 3):
+        """(column tile width, fused rows) chosen for this plan's shape."""
+        w, f = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(lib().t2sh_autotune(self._h, int(probe_iters), ctypes.byref(w), ctypes.byref(f)))
+        return int(w.value), bool(f.value)
 
     # -- kernel timing ----------------------------------------------------------------
     KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band"}

@@ -260,3 +260,49 @@ def test_solve_knee_slices_projected(T):
         e = nrmse(got[i], ref)
         print("knee slice", sl[i], "NRMSE", e)
         assert e < SOLVE_TOL
+
+
+def test_resumable_solve_equals_one_call(T):
+    rng, phi, mask, maps = random_problem(31, 2, 64, 48, 4, 16, 4, 1, frac=0.2)
+    y = c64(crandn(rng, 2, 4, 16, 64, 48) * mask[None, None] * 0.1)
+    kw = dict(block=8, lam=0.02, iters=25, seed=9)
+    with make_plan(T, phi, mask, maps, **kw) as p:
+        one = host(p.solve(y, T.KSPACE_TE))
+        p.solve_begin(y, T.KSPACE_TE)
+        assert p.solve_iterate(10) == 10
+        assert p.solve_iterate(4) == 14
+        assert p.solve_iterate(100) == 25
+        parts, res = p.solve_end(residual=True)
+        parts = host(parts)
+    assert np.array_equal(parts, one)
+    assert res.shape == (25,) and np.all(res > 0)
+
+
+def test_batch_of_uneven_scans_matches_single_solves(T):
+    shapes = [(2, 64, 48, 4, 16, 4, 1), (3, 96, 64, 3, 12, 4, 1), (1, 48, 48, 6, 10, 3, 2)]
+    plans, ks, singles = [], [], []
+    for i, (S, ny, nz, C, Tn, K, M) in enumerate(shapes):
+        rng, phi, mask, maps = random_problem(200 + i, S, ny, nz, C, Tn, K, M, frac=0.25)
+        ytil = c64(crandn(rng, S, C, K, ny, nz) * 0.05)
+        p = make_plan(T, phi, mask, maps, block=8, lam=0.01, iters=12 + 3 * i, seed=5 + i)
+        singles.append(host(p.solve(ytil, T.KSPACE_PROJ)))
+        plans.append(p)
+        ks.append(ytil)
+    outs = T.solve_batch(plans, ks)
+    for o, ref in zip(outs, singles):
+        assert np.array_equal(host(o), ref)
+    for p in plans:
+        p.close()
+
+
+def test_autotuned_plan_still_matches_oracle(T):
+    sh = synth.SINGLE_SLICE_64x48
+    phi, mask, maps, y = te_case(sh)
+    phi, maps = r32(phi, maps)
+    ys = y.astype(np.complex64).astype(np.complex128)
+    ref = O.fista(ys, "te", maps, mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
+    with make_plan(T, phi, mask, maps[None], block=sh.block, lam=sh.lam, iters=sh.iters, seed=sh.seed) as p:
+        colw, fused = p.autotune(probe_iters=-1)
+        assert colw in (4, 8) and fused in (False, True)
+        got = host(p.solve(c64(y[None]), T.KSPACE_TE))[0]
+    assert nrmse(got, ref) < SOLVE_TOL
