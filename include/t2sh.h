@@ -190,16 +190,32 @@ t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* k
                              void* const* alpha_out, void* stream);
 
 /*
- * t2sh_autotune -- choose, for the plan's problem shape, the column-pass tile width
- * (8 or 4 columns) and separate versus fused row kernels, by timing probe_iters
+ * t2sh_autotune -- choose, for the plan's problem shape, the column-pass variant
+ * (0: tiles of 8 columns moved by TMA, 1: tiles of 8 by cp.async, 2: tiles of 4 by
+ * cp.async) and separate versus fused row kernels, by timing probe_iters
  * iterations (default 3 when <= 0) of each candidate on the plan's buffers; the choice
  * is remembered per shape (and appended to the file named by the environment variable
  * T2SH_TUNE_CACHE, read back by later processes).  With probe_iters >= 0 a shape that is
  * already known is not timed again; probe_iters < 0 forces a new measurement.  Clobbers
  * the plan's FISTA state: call it before t2sh_solve_begin.  Synchronises the stream.
- * colw_out / fused_out (nullable) receive the choice.
+ * col_variant_out / fused_out (nullable) receive the choice.
  */
-t2sh_status t2sh_autotune(t2sh_plan_t plan, int32_t probe_iters, int32_t* colw_out, int32_t* fused_out);
+t2sh_status t2sh_autotune(t2sh_plan_t plan, int32_t probe_iters, int32_t* col_variant_out, int32_t* fused_out);
+
+/*
+ * t2sh_configure -- pin the plan's kernel choices instead of tuning them: col_variant as
+ * for t2sh_autotune (0, 1, 2; shapes a variant does not cover fall back to the generic
+ * kernels), fused_rows != 0 for the fused band kernel where it applies.  Not during a solve.
+ */
+t2sh_status t2sh_configure(t2sh_plan_t plan, int32_t col_variant, int32_t fused_rows);
+
+/*
+ * t2sh_sync -- synchronise the plan's stream and report failures of its asynchronous
+ * work: T2SH_ETIMEOUT if a bounded device wait (a TMA tile copy that did not complete
+ * within 2 s) made a kernel give up since the last call (the flag is then cleared),
+ * T2SH_ECUDA for a CUDA error.
+ */
+t2sh_status t2sh_sync(t2sh_plan_t plan);
 
 /* The step mu the plan uses (host float). */
 t2sh_status t2sh_get_step(t2sh_plan_t plan, float* step);

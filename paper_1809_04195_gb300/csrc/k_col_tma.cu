@@ -1,0 +1,263 @@
+// Column pass of the normal operator (DFT_y, Psi, IDFT_y) with its tiles moved by the
+// Tensor Memory Accelerator.  Persistent CTAs walk the (slice, coil, 8-column tile)
+// list; for each tile one thread issues two 3D tensor-map box copies that complete on
+// mbarriers: the K x ny x 8 block of the intermediate t and the P x ny x 8 block of
+// Psi.  The next tile's t block is requested as soon as the forward stage A has read the
+// current one, the next Psi block right after the Psi step, so both copies overlap the
+// remaining transform work.  Results go straight from registers to global memory.
+//
+// Transform layout (N = 16 R1): thread (w, j) of basis line k holds column w's
+// x[j + 16 q]; forward [R1, 16] and inverse [16, R1] two-stage transforms as in the
+// size-specialised kernels.  A half-warp spans the 8 columns x 2 consecutive j of one
+// basis line, the exchange lines are padded to a stride = 2 (mod 16) float2 and the
+// in-line layouts use odd strides, so every shared-memory access of the kernel is free
+// of bank conflicts.  Requires nz % 8 == 0, K <= 4, ny = N <= 256.
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "t2sh_device.cuh"
+
+namespace t2sh {
+
+template <int N>
+struct ColTma {
+  static constexpr int R1 = N / 16;
+  static constexpr int SF = ExLayout<R1>::SF;  // forward in-line stride (odd)
+  static constexpr int SI = 17;                // inverse in-line stride (odd)
+  static constexpr int LINE = ExLayout<R1>::LINE;
+  static constexpr int LS = LINE + ((18 - LINE % 16) % 16);  // = 2 (mod 16)
+  static constexpr size_t off_ex = ((size_t)N * 8 + 127) / 128 * 128;                       // bytes
+  static constexpr size_t off_t = (off_ex + (size_t)32 * LS * 8 + 127) / 128 * 128;
+  static constexpr size_t off_psi = off_t + (size_t)4 * N * 8 * 8;
+  static size_t smem(int P) { return off_psi + (size_t)P * N * 8 * 4 + 64; }
+};
+
+template <int N>
+__global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constant__ CUtensorMap tm_t,
+                                                   const __grid_constant__ CUtensorMap tm_psi,
+                                                   const float2* __restrict__ tw_g, float2* t, int ntz, int ntiles) {
+  using CT = ColTma<N>;
+  constexpr int R1 = CT::R1, SF = CT::SF, SI = CT::SI, LS = CT::LS;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* ex = reinterpret_cast<float2*>(smem_raw + CT::off_ex);   // [k][w][LS]
+  float2* st = reinterpret_cast<float2*>(smem_raw + CT::off_t);    // [k][y][8] (TMA box)
+  float* ps = reinterpret_cast<float*>(smem_raw + CT::off_psi);    // [p][y][8] (TMA box)
+  const int nz = g.nz, NN = N * nz, K = g.K, P = g.P;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + (size_t)P * N * 8 * 4);
+  const int w = threadIdx.x & 7, jl = (threadIdx.x >> 3) & 1, k = (threadIdx.x >> 4) & 3, j = 2 * (threadIdx.x >> 6) + jl;
+  const bool live = k < K;
+  const unsigned bytes_t = (unsigned)(K * N * 8 * 8), bytes_p = (unsigned)(P * N * 8 * 4);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) {
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * 8;
+    mbar_expect_tx(&bars[0], bytes_t);
+    tma_load_3d(st, &tm_t, &bars[0], z0, 0, sc * K);
+    mbar_expect_tx(&bars[1], bytes_p);
+    tma_load_3d(ps, &tm_psi, &bars[1], z0, 0, 0);
+  }
+  unsigned ph_t = 0, ph_p = 0;
+  float2* exl = ex + (k * 8 + w) * LS;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * 8;
+    bool ok = mbar_wait_bounded(&bars[0], ph_t);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {  // record, then give copies in flight one more bounded wait
+        if (g.err) atomicExch(g.err, 1);
+        mbar_wait_bounded(&bars[0], ph_t);
+        mbar_wait_bounded(&bars[1], ph_p);
+      }
+      return;
+    }
+    ph_t ^= 1;
+    // forward stage A: DFT_R1 of x[j + 16 q]
+    if (live) {
+      const float2* sp = st + (k * N) * 8 + w;
+      float2 a[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * 8];
+      dft_r<R1, false>(a);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) exl[j * SF + q] = a[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && nxt < ntiles) {  // the t block is consumed: fetch the next one
+      const int sn = nxt / ntz, zn = (nxt - sn * ntz) * 8;
+      fence_proxy_async_smem();
+      mbar_expect_tx(&bars[0], bytes_t);
+      tma_load_3d(st, &tm_t, &bars[0], zn, 0, sn * K);
+    }
+    // forward stage B: twiddle, DFT_16 -> X[j + R1 q] at [q][j]
+    if (live && j < R1) {
+      float2 b[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
+#pragma unroll
+      for (int q = 1; q < 16; ++q) b[q] = twiddle_mul<false>(b[q], tw[q * j]);
+      dft16<false>(b);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) exl[q * SF + j] = b[q];
+    }
+    ok = mbar_wait_bounded(&bars[1], ph_p);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        if (g.err) atomicExch(g.err, 1);
+        mbar_wait_bounded(&bars[1], ph_p);
+        if (nxt < ntiles) mbar_wait_bounded(&bars[0], ph_t);
+      }
+      return;
+    }
+    ph_p ^= 1;
+    // space-time kernel at the points (ky, c0 .. c0 + 3) of the tile
+    for (int pg = threadIdx.x; pg < 2 * N; pg += blockDim.x) {
+      const int c0 = (pg & 1) * 4, ky = pg >> 1;
+      const int pos = (ky / R1) * SF + (ky % R1);
+      float2 v[4][4], u[4][4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          v[l][c] = (l < K) ? ex[(l * 8 + c0 + c) * LS + pos] : make_float2(0.f, 0.f);
+          u[l][c] = make_float2(0.f, 0.f);
+        }
+      int pp = 0;
+#pragma unroll
+      for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+        for (int b_ = a_; b_ < 4; ++b_)
+          if (b_ < K) {
+            const float4 q4 = *reinterpret_cast<const float4*>(ps + (pp * N + ky) * 8 + c0);
+            const float pv[4] = {q4.x, q4.y, q4.z, q4.w};
+            ++pp;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              u[a_][c].x = fmaf(pv[c], v[b_][c].x, u[a_][c].x);
+              u[a_][c].y = fmaf(pv[c], v[b_][c].y, u[a_][c].y);
+              if (b_ != a_) {
+                u[b_][c].x = fmaf(pv[c], v[a_][c].x, u[b_][c].x);
+                u[b_][c].y = fmaf(pv[c], v[a_][c].y, u[b_][c].y);
+              }
+            }
+          }
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        if (l < K)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) ex[(l * 8 + c0 + c) * LS + pos] = u[l][c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && nxt < ntiles) {  // the Psi block is consumed: fetch the next one
+      const int zn = (nxt - (nxt / ntz) * ntz) * 8;
+      fence_proxy_async_smem();
+      mbar_expect_tx(&bars[1], bytes_p);
+      tma_load_3d(ps, &tm_psi, &bars[1], zn, 0, 0);
+    }
+    // inverse stage A': IDFT_16 of X[j + R1 q], result to [j][r1] (stride 17)
+    float2 b[16];
+    if (live && j < R1) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
+      dft16<true>(b);
+    }
+    __syncthreads();
+    if (live && j < R1) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) exl[j * SI + q] = b[q];
+    }
+    __syncthreads();
+    // inverse stage B': twiddle, IDFT_R1 -> y = j + 16 q, straight to global memory
+    if (live) {
+      float2 a[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) a[q] = twiddle_mul<true>(exl[q * SI + j], tw[q * j]);
+      dft_r<R1, true>(a);
+      float2* ob = t + ((long long)sc * K + k) * NN + z0 + w;
+#pragma unroll
+      for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
+    }
+    __syncthreads();
+  }
+}
+
+namespace {
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+template <int N>
+cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
+  using CT = ColTma<N>;
+  EncodeFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tm_t, tm_psi;
+  const cuuint64_t dt[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.S * g.C * g.K};
+  const cuuint64_t st_t[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)N * g.nz * 8};
+  const cuuint32_t bt[3] = {8, (cuuint32_t)N, (cuuint32_t)g.K};
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&tm_t, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, t, dt, st_t, bt, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorNotSupported;
+  const cuuint64_t dp[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.P};
+  const cuuint64_t sp[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)N * g.nz * 4};
+  const cuuint32_t bp[3] = {8, (cuuint32_t)N, (cuuint32_t)g.P};
+  if (enc(&tm_psi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(psi), dp, sp, bp, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorNotSupported;
+  const size_t sm = CT::smem(g.P);
+  static int nsm = 0;
+  if (!nsm) {
+    cudaError_t e = cudaFuncSetAttribute(k_col_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::smem(10));
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  const int ntz = g.nz / 8;
+  const long long ntiles = (long long)g.S * g.C * ntz;
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ntiles, nsm);
+  k_col_tma<N><<<grid, 512, sm, st>>>(g, tm_t, tm_psi, tw, t, ntz, (int)ntiles);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_col_normal_tma(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
+  if (g.K > 4 || g.nz % 8 != 0) return cudaErrorNotSupported;
+  switch (g.ny) {
+    case 48: return col_tma_go<48>(g, tw_y, psi, t, st);
+    case 64: return col_tma_go<64>(g, tw_y, psi, t, st);
+    case 96: return col_tma_go<96>(g, tw_y, psi, t, st);
+    case 128: return col_tma_go<128>(g, tw_y, psi, t, st);
+    case 160: return col_tma_go<160>(g, tw_y, psi, t, st);
+    case 192: return col_tma_go<192>(g, tw_y, psi, t, st);
+    case 240: return col_tma_go<240>(g, tw_y, psi, t, st);
+    case 256: return col_tma_go<256>(g, tw_y, psi, t, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace t2sh

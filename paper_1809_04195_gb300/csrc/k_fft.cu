@@ -450,6 +450,10 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
   switch (mode) {
     case COL_NORMAL:
       if (tin != tout) return cudaErrorInvalidValue;  // the normal-operator pass works in place
+      if (g.colvar == 0) {
+        const cudaError_t et = launch_col_normal_tma(g, tw_y, psi, tout, st);
+        if (et != cudaErrorNotSupported) return et;
+      }
       {
         const cudaError_t ef = launch_col_normal_fast(g, tw_y, psi, tout, st);
         if (ef != cudaErrorNotSupported) return ef;

@@ -409,7 +409,7 @@ static cudaError_t col_fast_w(const Geom& g, const float2* tw_y, const float* ps
 }
 
 cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
-  return g.colw == 4 ? col_fast_w<4>(g, tw_y, psi, t, st) : col_fast_w<kColW>(g, tw_y, psi, t, st);
+  return g.colvar == 2 ? col_fast_w<4>(g, tw_y, psi, t, st) : col_fast_w<kColW>(g, tw_y, psi, t, st);
 }
 
 }  // namespace t2sh

@@ -314,7 +314,7 @@ t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* ma
   g.ny = d.ny; g.nz = d.nz; g.P = d.nbasis * (d.nbasis + 1) / 2;
   g.gsign = (((d.ny / 2) + (d.nz / 2)) & 1) ? -1.f : 1.f;
   g.inv_sqrt_n = (float)(1.0 / std::sqrt((double)d.ny * d.nz));
-  g.colw = 8;
+  g.colvar = 0;
   p->fused_rows = (d.flags & T2SH_FUSED_ROWS) != 0;
   if (!make_fft_plan(d.ny, p->py) || !make_fft_plan(d.nz, p->pz)) {
     delete p;
@@ -344,6 +344,7 @@ t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* ma
   ALLOC(p->res, sizeof(double) * 2 * (size_t)(d.iters > 0 ? d.iters : 1));
   ALLOC(p->red, 64);
 #undef ALLOC
+  g.err = reinterpret_cast<int*>(p->red + 8);
   // twiddles exp(-2 pi i m / n), computed in double
   std::vector<float2> tw(std::max(d.ny, d.nz));
   auto fill_tw = [&](int n) {
@@ -425,6 +426,28 @@ t2sh_status t2sh_timing_read(t2sh_plan_t p, int32_t cls, int64_t* launches, doub
   }
   *launches = p->launches[cls];
   *ms = tot;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_configure(t2sh_plan_t p, int32_t col_variant, int32_t fused_rows) {
+  T2SH_REQ(p, "NULL plan");
+  T2SH_REQ(col_variant >= 0 && col_variant <= 2, "col_variant must be 0, 1 or 2");
+  T2SH_REQ(!p->begun || p->iter_done == p->d.iters, "configure must not interrupt a solve in progress");
+  p->g.colvar = col_variant;
+  p->fused_rows = fused_rows != 0;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_sync(t2sh_plan_t p) {
+  T2SH_REQ(p, "NULL plan");
+  T2SH_CK(cudaStreamSynchronize(p->st));
+  int flag = 0;
+  T2SH_CK(cudaMemcpy(&flag, p->g.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    T2SH_CK(cudaMemset(p->g.err, 0, sizeof(int)));
+    set_err("a bounded device wait ran out (a tile copy did not complete in time)");
+    return T2SH_ETIMEOUT;
+  }
   return T2SH_OK;
 }
 
@@ -746,9 +769,9 @@ extern "C" t2sh_status t2sh_autotune(t2sh_plan_t p, int32_t probe_iters, int32_t
     tune_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end() && probe_iters >= 0) {
-      p->g.colw = it->second.first;
+      p->g.colvar = it->second.first;
       p->fused_rows = it->second.second != 0;
-      if (colw_out) *colw_out = p->g.colw;
+      if (colw_out) *colw_out = p->g.colvar;
       if (fused_out) *fused_out = p->fused_rows ? 1 : 0;
       return T2SH_OK;
     }
@@ -767,11 +790,11 @@ extern "C" t2sh_status t2sh_autotune(t2sh_plan_t p, int32_t probe_iters, int32_t
   const bool timing = p->timing;
   p->timing = false;
   float best = 1e30f;
-  int bw = 8, bf = 0;
+  int bw = 0, bf = 0;
   t2sh_status st = T2SH_OK;
-  for (int colw : {8, 4}) {
+  for (int colw : {0, 1, 2}) {
     for (int fused = 0; fused <= (band_fused_supported(p->g, d.block) ? 1 : 0); ++fused) {
-      p->g.colw = colw;
+      p->g.colvar = colw;
       p->fused_rows = fused != 0;
       p->begun = true;
       p->record_res = false;
@@ -805,7 +828,7 @@ extern "C" t2sh_status t2sh_autotune(t2sh_plan_t p, int32_t probe_iters, int32_t
     if (g_err.empty()) set_err("autotune: a CUDA call failed");
     return st;
   }
-  p->g.colw = bw;
+  p->g.colvar = bw;
   p->fused_rows = bf != 0;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
             "t2sh_solve_batch": [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i32),
                                  ctypes.POINTER(_vp), _vp],
             "t2sh_autotune": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+            "t2sh_sync": [_vp],
+            "t2sh_configure": [_vp, _i32, _i32],
             "t2sh_timing_read": [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
@@ -288,10 +290,20 @@ class Plan:
         return (out, res) if residual else out
 
     def autotune(self, probe_iters: int = 3):
-        """(column tile width, fused rows) chosen for this plan's shape."""
+        """(column-pass variant 0 TMA / 1 cp.async x8 / 2 cp.async x4, fused rows) chosen
+        for this plan's shape."""
         w, f = ctypes.c_int32(0), ctypes.c_int32(0)
         _check(lib().t2sh_autotune(self._h, int(probe_iters), ctypes.byref(w), ctypes.byref(f)))
         return int(w.value), bool(f.value)
+
+    def configure(self, col_variant: int, fused_rows: bool = False):
+        """Pin the column-pass variant (0 TMA, 1 cp.async x8, 2 cp.async x4) and row fusion."""
+        _check(lib().t2sh_configure(self._h, int(col_variant), 1 if fused_rows else 0))
+
+    def sync(self):
+        """Synchronise the plan's stream; raises T2shError(ETIMEOUT) if a bounded device
+        wait ran out since the last call."""
+        _check(lib().t2sh_sync(self._h))
 
     # -- kernel timing ----------------------------------------------------------------
     KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band"}
