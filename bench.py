@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--slices", type=int, default=None, help="fewer slices (profiling runs only)")
     ap.add_argument("--iters", type=int, default=None, help="fewer iterations (profiling runs only)")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32",
+                    help="mixed: column DFTs as split-BF16 GEMMs on the tensor cores (FP32 accumulation)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -232,8 +234,9 @@ def run_ours(args):
     from paper_1809_04195_gb300.workload import make_scan
     phi_d, mask_d, maps_d, ytil_d = make_scan(sh, S, dev)
     out_d = torch.empty((S, 1, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    prec = t2sh.MIXED_BF16 if args.precision == "mixed" else t2sh.FP32
     dims = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, block=sh.block,
-                          lam=sh.lam, iters=iters, seed=sh.seed)
+                          lam=sh.lam, iters=iters, seed=sh.seed, precision=prec)
     N = sh.ny * sh.nz
     units = S * iters
 
@@ -279,7 +282,7 @@ def run_ours(args):
         hy = ytil_d.cpu().pin_memory()
         hout = torch.empty(out_d.shape, dtype=torch.complex64).pin_memory()
         hd = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, block=sh.block,
-                            lam=sh.lam, iters=iters, seed=sh.seed, flags=t2sh.HOST_IO)
+                            lam=sh.lam, iters=iters, seed=sh.seed, precision=prec, flags=t2sh.HOST_IO)
 
         def hstep():
             p = t2sh.Plan(hd, hphi, hmask, hmaps)
@@ -322,9 +325,10 @@ def run_ours(args):
     launches = sum(v["launches"] for v in kern.values()) + 2 * args.steps  # + maps/Psi kernels of t2sh_plan
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "full_scan_s": ms / args.steps / 1000.0,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == t2sh.FP32 else "f32 + bf16x3 (column DFTs on tensor cores, f32 accumulate)",
             "data": "synthetic (seeded 3D ellipsoid knee phantom, smooth coil maps, variable-density masks)",
-            "config": config_dict(sh, S, iters, world), "roofline": roof, "gpu_launches": launches,
+            "config": {**config_dict(sh, S, iters, world), "precision": args.precision}, "roofline": roof, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": e2e}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sh)

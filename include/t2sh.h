@@ -50,7 +50,15 @@ typedef enum {
   T2SH_EBUSY = 6         /* the plan is in use                                         */
 } t2sh_status;
 
-/* t2sh_dims.precision */
+/*
+ * t2sh_dims.precision.  T2SH_FP32: every step in single precision.  T2SH_MIXED_BF16: the
+ * column pass of the normal operator (DFT along ky, the space-time kernel Psi of Sec. IV.B,
+ * inverse DFT) runs its DFTs as GEMMs on the tensor cores with operands split into BF16
+ * hi/lo pairs and FP32 accumulation (about 16 significant bits per product); the stated
+ * accuracy of this path is a per-slice NRMSE <= 1e-3 of the solve.  Shapes the tensor-core
+ * kernel does not cover (ny not 16 R1 with R1 in {3,4,6,8,10,12,15,16}, nz % 4 != 0 or
+ * nbasis > 4) use the FP32 column pass.  The paper has no mixed-precision variant.
+ */
 enum { T2SH_FP32 = 0, T2SH_MIXED_BF16 = 1 };
 
 /* kform argument: layout of k-space data */
@@ -82,7 +90,7 @@ typedef struct {
   uint64_t seed;           /* seed of the random LLR shifts                              */
   float step;              /* > 0: FISTA step mu; <= 0: the plan computes mu = 1/L with
                               L = max_n lambda_max Psi(n) * max_p lambda_max S(p)^H S(p) */
-  int32_t precision;       /* T2SH_FP32 (T2SH_MIXED_BF16: reserved, T2SH_EUNSUPPORTED)   */
+  int32_t precision;       /* T2SH_FP32 or T2SH_MIXED_BF16 (other values: T2SH_EINVAL)  */
   uint32_t flags;          /* T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64 | T2SH_FUSED_ROWS */
 } t2sh_dims;
 
@@ -192,7 +200,8 @@ t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* k
 /*
  * t2sh_autotune -- choose, for the plan's problem shape, the column-pass variant
  * (0: tiles of 8 columns moved by TMA, 1: tiles of 8 by cp.async, 2: tiles of 4 by
- * cp.async) and separate versus fused row kernels, by timing probe_iters
+ * cp.async; a T2SH_MIXED_BF16 plan keeps its tensor-core column pass, variant 3) and
+ * separate versus fused row kernels, by timing probe_iters
  * iterations (default 3 when <= 0) of each candidate on the plan's buffers; the choice
  * is remembered per shape (and appended to the file named by the environment variable
  * T2SH_TUNE_CACHE, read back by later processes).  With probe_iters >= 0 a shape that is
@@ -204,8 +213,9 @@ t2sh_status t2sh_autotune(t2sh_plan_t plan, int32_t probe_iters, int32_t* col_va
 
 /*
  * t2sh_configure -- pin the plan's kernel choices instead of tuning them: col_variant as
- * for t2sh_autotune (0, 1, 2; shapes a variant does not cover fall back to the generic
- * kernels), fused_rows != 0 for the fused band kernel where it applies.  Not during a solve.
+ * for t2sh_autotune (0, 1, 2, or 3 for the tensor-core mixed-precision column pass; shapes
+ * a variant does not cover fall back to the FP32 kernels), fused_rows != 0 for the fused
+ * band kernel where it applies.  Not during a solve.
  */
 t2sh_status t2sh_configure(t2sh_plan_t plan, int32_t col_variant, int32_t fused_rows);
 

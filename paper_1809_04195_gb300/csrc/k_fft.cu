@@ -450,7 +450,11 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
   switch (mode) {
     case COL_NORMAL:
       if (tin != tout) return cudaErrorInvalidValue;  // the normal-operator pass works in place
-      if (g.colvar == 0) {
+      if (g.colvar == 3) {
+        const cudaError_t ec = launch_col_normal_tc(g, tw_y, psi, tout, st);
+        if (ec != cudaErrorNotSupported) return ec;
+      }
+      if (g.colvar == 0 || g.colvar == 3) {
         const cudaError_t et = launch_col_normal_tma(g, tw_y, psi, tout, st);
         if (et != cudaErrorNotSupported) return et;
       }

@@ -125,10 +125,7 @@ t2sh_status validate(const t2sh_dims* d) {
   T2SH_REQ(d->iters >= 0, "iters must be >= 0");
   T2SH_REQ(std::isfinite(d->lambda) && d->lambda >= 0.f, "lambda must be finite and >= 0");
   T2SH_REQ(std::isfinite(d->step), "step must be finite");
-  if (d->precision != T2SH_FP32) {
-    set_err("precision %d not implemented", d->precision);
-    return T2SH_EUNSUPPORTED;
-  }
+  T2SH_REQ(d->precision == T2SH_FP32 || d->precision == T2SH_MIXED_BF16, "precision must be T2SH_FP32 or T2SH_MIXED_BF16");
   T2SH_REQ((d->flags & ~(T2SH_NO_SHIFT | T2SH_HOST_IO | T2SH_EIG_FP64 | T2SH_FUSED_ROWS)) == 0,
            "unknown flag bits");
   Geom g{};
@@ -314,7 +311,7 @@ t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* ma
   g.ny = d.ny; g.nz = d.nz; g.P = d.nbasis * (d.nbasis + 1) / 2;
   g.gsign = (((d.ny / 2) + (d.nz / 2)) & 1) ? -1.f : 1.f;
   g.inv_sqrt_n = (float)(1.0 / std::sqrt((double)d.ny * d.nz));
-  g.colvar = 0;
+  g.colvar = d.precision == T2SH_MIXED_BF16 ? 3 : 0;
   p->fused_rows = (d.flags & T2SH_FUSED_ROWS) != 0;
   if (!make_fft_plan(d.ny, p->py) || !make_fft_plan(d.nz, p->pz)) {
     delete p;
@@ -431,7 +428,7 @@ t2sh_status t2sh_timing_read(t2sh_plan_t p, int32_t cls, int64_t* launches, doub
 
 t2sh_status t2sh_configure(t2sh_plan_t p, int32_t col_variant, int32_t fused_rows) {
   T2SH_REQ(p, "NULL plan");
-  T2SH_REQ(col_variant >= 0 && col_variant <= 2, "col_variant must be 0, 1 or 2");
+  T2SH_REQ(col_variant >= 0 && col_variant <= 3, "col_variant must be 0, 1, 2 or 3");
   T2SH_REQ(!p->begun || p->iter_done == p->d.iters, "configure must not interrupt a solve in progress");
   p->g.colvar = col_variant;
   p->fused_rows = fused_rows != 0;
@@ -729,7 +726,7 @@ bool g_tune_loaded = false;
 
 std::string tune_key(const t2sh_dims& d) {
   char b[128];
-  snprintf(b, sizeof(b), "%d %d %d %d %d %d", d.ny, d.nz, d.ncoils, d.nbasis, d.nmaps, d.block);
+  snprintf(b, sizeof(b), "%d %d %d %d %d %d %d", d.ny, d.nz, d.ncoils, d.nbasis, d.nmaps, d.block, d.precision);
   return b;
 }
 
@@ -740,11 +737,12 @@ void tune_load() {
   if (!f) return;
   FILE* fp = std::fopen(f, "r");
   if (!fp) return;
-  int a[8];
-  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6], &a[7]) == 8) {
+  int a[9];
+  while (std::fscanf(fp, "%d %d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6], &a[7],
+                     &a[8]) == 9) {
     char b[128];
-    snprintf(b, sizeof(b), "%d %d %d %d %d %d", a[0], a[1], a[2], a[3], a[4], a[5]);
-    g_tune[b] = {a[6], a[7]};
+    snprintf(b, sizeof(b), "%d %d %d %d %d %d %d", a[0], a[1], a[2], a[3], a[4], a[5], a[6]);
+    if (a[7] >= 0 && a[7] <= 3) g_tune[b] = {a[7], a[8]};
   }
   std::fclose(fp);
 }
@@ -792,7 +790,9 @@ extern "C" t2sh_status t2sh_autotune(t2sh_plan_t p, int32_t probe_iters, int32_t
   float best = 1e30f;
   int bw = 0, bf = 0;
   t2sh_status st = T2SH_OK;
-  for (int colw : {0, 1, 2}) {
+  // the mixed-precision column pass is the precision's choice, not a tuning candidate
+  const std::vector<int> cols = d.precision == T2SH_MIXED_BF16 ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
+  for (int colw : cols) {
     for (int fused = 0; fused <= (band_fused_supported(p->g, d.block) ? 1 : 0); ++fused) {
       p->g.colvar = colw;
       p->fused_rows = fused != 0;

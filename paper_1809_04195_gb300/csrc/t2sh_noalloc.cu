@@ -114,7 +114,7 @@ extern "C" t2sh_status t2sh_normal_op_noalloc(const t2sh_dims* dims, const float
   g.ny = d.ny; g.nz = d.nz; g.P = P;
   g.gsign = (((d.ny / 2) + (d.nz / 2)) & 1) ? -1.f : 1.f;
   g.inv_sqrt_n = (float)(1.0 / sqrt((double)N));
-  g.colvar = 0;
+  g.colvar = d.precision == T2SH_MIXED_BF16 ? 3 : 0;
   g.err = reinterpret_cast<int*>(red + 8);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 

@@ -33,7 +33,8 @@ struct Geom {
   float gsign;         // (-1)^(ny/2 + nz/2): global sign of the centred DFT
   float inv_sqrt_n;    // 1 / sqrt(ny nz)
   int colvar;          // normal-operator column pass: 0 TMA tiles of 8 columns, 1 cp.async
-                       // tiles of 8, 2 cp.async tiles of 4 (size-specialised kernels)
+                       // tiles of 8, 2 cp.async tiles of 4 (size-specialised kernels),
+                       // 3 tensor-core DFT-as-GEMM in split BF16 (mixed precision)
   int* err;            // nullable device flag: set to 1 when a bounded wait ran out
 };
 
@@ -82,6 +83,7 @@ cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, 
 cudaError_t launch_row_fast(const Geom& g, RowMode mode, const float2* tw_z, const float2* maps, const float2* x,
                             float2* t, float2* out, cudaStream_t st);
 cudaError_t launch_col_normal_fast(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
+cudaError_t launch_col_normal_tc(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 cudaError_t launch_col_normal_tma(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 
 // fused row work of one FISTA iteration (k_fused.cu)

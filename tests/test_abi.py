@@ -56,7 +56,7 @@ def test_workspace_bytes_formula(lib):
     (dict(nmaps=3), t2sh.EINVAL),
     (dict(block=0), t2sh.EINVAL),
     (dict(nechoes=3), t2sh.EINVAL),      # T < K
-    (dict(precision=t2sh.MIXED_BF16), t2sh.EUNSUPPORTED),
+    (dict(precision=2), t2sh.EINVAL),     # neither FP32 nor MIXED_BF16
     (dict(flags=0x80), t2sh.EINVAL),
     (dict(flags=0x10), t2sh.EINVAL),
 ])
@@ -67,6 +67,13 @@ def test_invalid_dims_rejected(lib, kw, status):
     n = ctypes.c_size_t(0)
     assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == status
     assert len(t2sh.last_error()) > 0
+
+
+def test_mixed_precision_dims_accepted(lib):
+    d = t2sh.make_dims(256, 160, 12, 80, 4, nslices=2, block=8, iters=10, precision=t2sh.MIXED_BF16)
+    n = ctypes.c_size_t(0)
+    assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == t2sh.OK
+    assert n.value == t2sh.workspace_bytes(t2sh.make_dims(256, 160, 12, 80, 4, nslices=2, block=8, iters=10))
 
 
 def test_null_arguments_rejected(lib):
