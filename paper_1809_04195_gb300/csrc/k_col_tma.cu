@@ -189,28 +189,26 @@ __global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constan
   }
 }
 
-namespace {
-using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+TmaEncodeFn tma_encode_fn() {
+  static TmaEncodeFn fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
+      fn = reinterpret_cast<TmaEncodeFn>(p);
     cudaGetLastError();
   });
   return fn;
 }
 
+namespace {
 template <int N>
 cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
   using CT = ColTma<N>;
-  EncodeFn enc = encode_fn();
+  TmaEncodeFn enc = tma_encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tm_t, tm_psi;
   const cuuint64_t dt[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.S * g.C * g.K};
