@@ -13,8 +13,11 @@
 
 namespace t2sh {
 
+// The K <= 4 float32 variant is held to 80 registers so that three CTAs share an SM and
+// the single-thread eigen-steps of one band overlap the memory phases of the others.
 template <int KC, bool FISTA, typename ET>
-__global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x, float2* z,
+__global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1)
+    k_llr(Geom g, FistaArgs a, float2* x, float2* z,
                                                 const float2* __restrict__ grad, const float2* __restrict__ aty) {
   extern __shared__ float2 smem[];
   const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, M = g.M, b = a.b;
@@ -28,6 +31,7 @@ __global__ void __launch_bounds__(kThreads) k_llr(Geom g, FistaArgs a, float2* x
 
   // 1. gather the band (gradient step fused for FISTA), two pixels per float4
   const int nel2 = (M * K * rb * nz) >> 1;
+#pragma unroll 4
   for (int e2 = threadIdx.x; e2 < nel2; e2 += kThreads) {
     const int e = 2 * e2;
     const int zz = e % nz;
