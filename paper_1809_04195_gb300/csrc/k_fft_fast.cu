@@ -92,6 +92,15 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
     for (int q = 0; q < 16; ++q) acc[m][q] = make_float2(0.f, 0.f);
   }
   float2* exl = ex + L * LINE;
+  // Stage B has R1 < 16 work items per line: they are packed onto consecutive threads
+  // (item (Lb, jb) on thread Lb * R1 + jb) so that whole warps idle instead of 16 - R1
+  // lanes of every line's half-warp.
+  constexpr bool kPack = R1 < 16;
+  const int Lb = kPack ? (int)threadIdx.x / R1 : L;
+  const int jb = kPack ? (int)threadIdx.x - Lb * R1 : j;
+  const int kb = Lb / kRowRB, rbb = Lb - kb * kRowRB;
+  const bool liveb = (kPack ? ((int)threadIdx.x < NL * R1) : (j < R1)) && kb < K && rbb < rb;
+  const float2* exb = ex + Lb * LINE;
 
   for (int c = 0; c < g.C; ++c) {
     const int buf = c & 1;
@@ -120,35 +129,36 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
 #pragma unroll
     for (int q = 0; q < R1; ++q) exl[j * SF + q] = a[q];
     __syncthreads();
-    if (j < R1 && live) {
+    if (liveb) {
       float2 b[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
+      for (int q = 0; q < 16; ++q) b[q] = exb[q * SF + jb];
 #pragma unroll
-      for (int q = 1; q < 16; ++q) b[q] = (MODE == ROW_FWD) ? twiddle_mul<false>(b[q], tw[q * j]) : twiddle_mul<true>(b[q], tw[q * j]);
+      for (int q = 1; q < 16; ++q) b[q] = (MODE == ROW_FWD) ? twiddle_mul<false>(b[q], tw[q * jb]) : twiddle_mul<true>(b[q], tw[q * jb]);
       if (MODE == ROW_FWD) {
         dft16<false>(b);
-        float2* tp = t + ((long long)(s * g.C + c) * K + k) * NN + (long long)(y0 + r) * N + j;
+        float2* tp = t + ((long long)(s * g.C + c) * K + kb) * NN + (long long)(y0 + rbb) * N + jb;
 #pragma unroll
         for (int q = 0; q < 16; ++q) tp[R1 * q] = b[q];
       } else {
         dft16<true>(b);
+        const float2* mrowb = mst + buf * MC * kRowRB * N + rbb * N;
 #pragma unroll
         for (int m = 0; m < MC; ++m)
           if (m < M) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) cfmac(acc[m][q], mrow[m * kRowRB * N + j + R1 * q], b[q]);
+            for (int q = 0; q < 16; ++q) cfmac(acc[m][q], mrowb[m * kRowRB * N + jb + R1 * q], b[q]);
           }
       }
     }
     __syncthreads();
   }
   cp_async_wait<0>();
-  if (MODE == ROW_ADJ && j < R1 && live) {
+  if (MODE == ROW_ADJ && liveb) {
 #pragma unroll
     for (int m = 0; m < MC; ++m)
       if (m < M) {
-        float2* op = out + ((long long)(s * M + m) * K + k) * NN + (long long)(y0 + r) * N + j;
+        float2* op = out + ((long long)(s * M + m) * K + kb) * NN + (long long)(y0 + rbb) * N + jb;
 #pragma unroll
         for (int q = 0; q < 16; ++q) op[R1 * q] = acc[m][q];
       }

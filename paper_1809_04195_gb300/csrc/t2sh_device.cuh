@@ -271,8 +271,19 @@ __device__ __forceinline__ void fft_lines(float2* buf, int ld, int nbatch, const
 // when the off-diagonal mass is below (eps^2) of the diagonal mass.
 // ---------------------------------------------------------------------------------
 template <typename T> struct JacobiTol;
-template <> struct JacobiTol<double> { static constexpr double rel2 = 1e-30; };
-template <> struct JacobiTol<float> { static constexpr float rel2 = 1e-13f; };
+// rel2: stop when off-diagonal^2 < rel2 * diagonal^2; pivot2: skip a rotation whose
+// |a_pq|^2 is at most this (float32: below the normal range, where rsqrt is not exact)
+template <> struct JacobiTol<double> { static constexpr double rel2 = 1e-30, pivot2 = 0.0; };
+template <> struct JacobiTol<float> { static constexpr float rel2 = 1e-13f, pivot2 = 1e-36f; };
+
+// Reciprocal square root and reciprocal for the rotation parameters.  Any unitary
+// rotation that zeroes the pivot serves Jacobi, and the LLR step re-orthonormalises the
+// eigenvectors and recomputes the eigenvalues afterwards, so the float32 variant takes
+// the hardware approximations; float64 stays exact.
+__device__ __forceinline__ float jac_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double jac_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float jac_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double jac_rcp(double x) { return 1.0 / x; }
 
 template <typename T, int K>
 __device__ __forceinline__ void herm_jacobi(T (&ar)[K][K], T (&ai)[K][K], T (&vr)[K][K], T (&vi)[K][K],
@@ -299,10 +310,10 @@ __device__ __forceinline__ void herm_jacobi(T (&ar)[K][K], T (&ai)[K][K], T (&vr
       for (int q = p + 1; q < K; ++q) {
         const T xr = ar[p][q], xi = ai[p][q];
         const T r2 = xr * xr + xi * xi;
-        if (r2 > T(0)) {
-          const T r = sqrt(r2);
+        if (r2 > JacobiTol<T>::pivot2) {
+          const T ir = jac_rsqrt(r2), r = r2 * ir;
           // phase: column q *= d, row q *= conj(d), d = conj(a_pq) / |a_pq|
-          const T dr = xr / r, di = -xi / r;
+          const T dr = xr * ir, di = -xi * ir;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             if (k != q) {
@@ -319,10 +330,17 @@ __device__ __forceinline__ void herm_jacobi(T (&ar)[K][K], T (&ai)[K][K], T (&vr
             vr[k][q] = yr; vi[k][q] = yi;
           }
           // a_pq is now the real r: real rotation on rows/columns p, q
-          const T theta = (ar[q][q] - ar[p][p]) / (T(2) * r);
-          T t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
+          const T theta = (ar[q][q] - ar[p][p]) * (T(0.5) * ir);
+          const T at = fabs(theta);
+          T t;
+          if (at > T(1e18)) {  // theta^2 would overflow float32: t = 1 / (2 |theta|) to first order
+            t = T(0.5) / at;
+          } else {
+            const T u = at * at + T(1);
+            t = jac_rcp(at + u * jac_rsqrt(u));
+          }
           if (theta < T(0)) t = -t;
-          const T c = T(1) / sqrt(t * t + T(1));
+          const T c = jac_rsqrt(t * t + T(1));
           const T s = t * c;
           ar[p][p] -= t * r;
           ar[q][q] += t * r;
