@@ -27,6 +27,20 @@ using Ex = ExLayout<R1>;
 // adjoint pass (its double-buffered t rows) and wherever 8 would not fit in shared
 // memory (N >= 240 or two map sets).
 // ------------------------------------------------------------------------------------
+// Padded strides (float2) of the row pass's exchange lines (LX) and staged map rows (MS).
+// The packed second stage reads R1 consecutive items from each of several lines per
+// half-warp; a stride congruent to R1 modulo 16 lays those windows side by side across
+// the banks.  MS stays even so that the 16-byte cp.async copies remain aligned.
+template <int N>
+struct RowPad {
+  static constexpr int R1 = N / 16;
+  static constexpr int LINE = ExLayout<R1>::LINE;
+  static constexpr int even_r1 = (R1 % 2 == 0) ? R1 : R1 + 1;
+  static constexpr int LX = (R1 < 16) ? LINE + ((R1 - LINE % 16) % 16 + 16) % 16 : LINE;
+  static constexpr int MS = (R1 < 16) ? N + ((even_r1 - N % 16) % 16 + 16) % 16 : N;
+  static_assert(MS % 2 == 0 && LX >= LINE && MS >= N, "row pass strides");
+};
+
 template <int N, int MC, int MODE>
 struct RowFastRB {
   static constexpr int value = (N >= 240 || MC == 2 || MODE == ROW_ADJ) ? 4 : 8;
@@ -37,7 +51,10 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
                                                  const float2* __restrict__ maps, const float2* __restrict__ x,
                                                  float2* __restrict__ t, float2* __restrict__ out) {
   constexpr int R1 = N / 16;
-  constexpr int LINE = Ex<R1>::LINE;
+  constexpr int LINE = RowPad<N>::LX;
+  // the adjoint keeps unpadded map rows: at N = 160 the padding would cost it its third
+  // CTA per SM (76.9 KB of shared memory against 76.8 KB)
+  constexpr int MS = (MODE == ROW_ADJ) ? N : RowPad<N>::MS;
   constexpr int SF = Ex<R1>::SF;
   extern __shared__ float2 smem[];
   const int NN = g.ny * N, K = g.K, M = g.M;
@@ -48,21 +65,22 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
   const int L = threadIdx.x >> 4;  // line: k * RB + r
   const int k = L / kRowRB, r = L - k * kRowRB;
   const bool live = (k < K) && (r < rb);
-  // shared memory: twiddles | exchange [NL][LINE] | maps stage x2 [MC][RB][N] | t stage x2 [NL][N]
+  // shared memory: twiddles | exchange [NL][LINE] | maps stage x2 [MC][RB][MS] | t stage x2 [NL][N]
   float2* tw = smem;
   float2* ex = tw + N;
   float2* mst = ex + NL * LINE;
-  float2* tst = mst + 2 * MC * kRowRB * N;
+  float2* tst = mst + 2 * MC * kRowRB * MS;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
 
   auto issue = [&](int c, int buf) {
     const float2* mp = maps + ((long long)(s * g.C + c) * M) * NN + (long long)y0 * N;
-    float2* md = mst + buf * MC * kRowRB * N;
+    float2* md = mst + buf * MC * kRowRB * MS;
     const int nm = M * rb * N / 2;
     for (int e2 = threadIdx.x; e2 < nm; e2 += blockDim.x) {
       const int e = 2 * e2;
       const int m = e / (rb * N), rem = e - m * rb * N;
-      cp_async16(md + m * kRowRB * N + rem, mp + (long long)m * NN + rem);
+      const int row = rem / N, col = rem - row * N;
+      cp_async16(md + (m * kRowRB + row) * MS + col, mp + (long long)m * NN + rem);
     }
     if (MODE == ROW_ADJ) {
       const float2* tp = t + ((long long)(s * g.C + c) * K) * NN + (long long)y0 * N;
@@ -108,7 +126,7 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    const float2* mrow = mst + buf * MC * kRowRB * N + r * N;
+    const float2* mrow = mst + buf * MC * kRowRB * MS + r * MS;
     float2 a[R1];
     if (MODE == ROW_FWD) {
 #pragma unroll
@@ -116,7 +134,7 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
         float2 v = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 0; m < MC; ++m)
-          if (m < M) cfma(v, mrow[m * kRowRB * N + j + 16 * q], xr[m][q]);
+          if (m < M) cfma(v, mrow[m * kRowRB * MS + j + 16 * q], xr[m][q]);
         a[q] = v;
       }
       dft_r<R1, false>(a);
@@ -142,12 +160,12 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
         for (int q = 0; q < 16; ++q) tp[R1 * q] = b[q];
       } else {
         dft16<true>(b);
-        const float2* mrowb = mst + buf * MC * kRowRB * N + rbb * N;
+        const float2* mrowb = mst + buf * MC * kRowRB * MS + rbb * MS;
 #pragma unroll
         for (int m = 0; m < MC; ++m)
           if (m < M) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) cfmac(acc[m][q], mrowb[m * kRowRB * N + jb + R1 * q], b[q]);
+            for (int q = 0; q < 16; ++q) cfmac(acc[m][q], mrowb[m * kRowRB * MS + jb + R1 * q], b[q]);
           }
       }
     }
@@ -330,7 +348,8 @@ constexpr int kColW = 8;  // columns per tile of the column pass
 template <int N, int MODE, int MC>
 static size_t row_fast_smem() {
   constexpr int R1 = N / 16, RB = RowFastRB<N, MC, MODE>::value, NL = 4 * RB;
-  return sizeof(float2) * ((size_t)N + NL * Ex<R1>::LINE + 2 * (size_t)MC * RB * N +
+  constexpr int MS = (MODE == ROW_ADJ) ? N : RowPad<N>::MS;
+  return sizeof(float2) * ((size_t)N + NL * RowPad<N>::LX + 2 * (size_t)MC * RB * MS +
                            (MODE == ROW_ADJ ? 2 * (size_t)NL * N : 0));
 }
 
