@@ -199,8 +199,9 @@ t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* k
 
 /*
  * t2sh_autotune -- choose, for the plan's problem shape, the column-pass variant
- * (0: tiles of 8 columns moved by TMA, 1: tiles of 8 by cp.async, 2: tiles of 4 by
- * cp.async; a T2SH_MIXED_BF16 plan keeps its tensor-core column pass, variant 3) and
+ * (0: tiles of 8 columns moved by TMA, 4: tiles of 4 by TMA, 1: tiles of 8 by cp.async,
+ * 2: tiles of 4 by cp.async; a T2SH_MIXED_BF16 plan keeps its tensor-core column pass,
+ * variant 3) and
  * separate versus fused row kernels, by timing probe_iters
  * iterations (default 3 when <= 0) of each candidate on the plan's buffers; the choice
  * is remembered per shape (and appended to the file named by the environment variable
@@ -213,7 +214,7 @@ t2sh_status t2sh_autotune(t2sh_plan_t plan, int32_t probe_iters, int32_t* col_va
 
 /*
  * t2sh_configure -- pin the plan's kernel choices instead of tuning them: col_variant as
- * for t2sh_autotune (0, 1, 2, or 3 for the tensor-core mixed-precision column pass; shapes
+ * for t2sh_autotune (0, 1, 2, 4, or 3 for the tensor-core mixed-precision column pass; shapes
  * a variant does not cover fall back to the FP32 kernels), fused_rows != 0 for the fused
  * band kernel where it applies.  Not during a solve.
  */

@@ -21,7 +21,7 @@
 
 namespace t2sh {
 
-template <int N>
+template <int N, int W>
 struct ColTma {
   static constexpr int R1 = N / 16;
   static constexpr int SF = ExLayout<R1>::SF;  // forward in-line stride (odd)
@@ -29,27 +29,29 @@ struct ColTma {
   static constexpr int LINE = ExLayout<R1>::LINE;
   static constexpr int LS = LINE + ((18 - LINE % 16) % 16);  // = 2 (mod 16)
   static constexpr size_t off_ex = ((size_t)N * 8 + 127) / 128 * 128;                       // bytes
-  static constexpr size_t off_t = (off_ex + (size_t)32 * LS * 8 + 127) / 128 * 128;
-  static constexpr size_t off_psi = off_t + (size_t)4 * N * 8 * 8;
-  static size_t smem(int P) { return off_psi + (size_t)P * N * 8 * 4 + 64; }
+  static constexpr size_t off_t = (off_ex + (size_t)4 * W * LS * 8 + 127) / 128 * 128;
+  static constexpr size_t off_psi = off_t + (size_t)4 * N * W * 8;
+  static size_t smem(int P) { return off_psi + (size_t)P * N * W * 4 + 64; }
 };
 
-template <int N>
-__global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constant__ CUtensorMap tm_t,
+template <int N, int W>
+__global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_constant__ CUtensorMap tm_t,
                                                    const __grid_constant__ CUtensorMap tm_psi,
                                                    const float2* __restrict__ tw_g, float2* t, int ntz, int ntiles) {
-  using CT = ColTma<N>;
+  using CT = ColTma<N, W>;
   constexpr int R1 = CT::R1, SF = CT::SF, SI = CT::SI, LS = CT::LS;
+  constexpr int WL = W == 8 ? 3 : 2;  // log2 W
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* ex = reinterpret_cast<float2*>(smem_raw + CT::off_ex);   // [k][w][LS]
-  float2* st = reinterpret_cast<float2*>(smem_raw + CT::off_t);    // [k][y][8] (TMA box)
-  float* ps = reinterpret_cast<float*>(smem_raw + CT::off_psi);    // [p][y][8] (TMA box)
+  float2* st = reinterpret_cast<float2*>(smem_raw + CT::off_t);    // [k][y][W] (TMA box)
+  float* ps = reinterpret_cast<float*>(smem_raw + CT::off_psi);    // [p][y][W] (TMA box)
   const int nz = g.nz, NN = N * nz, K = g.K, P = g.P;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + (size_t)P * N * 8 * 4);
-  const int w = threadIdx.x & 7, jl = (threadIdx.x >> 3) & 1, k = (threadIdx.x >> 4) & 3, j = 2 * (threadIdx.x >> 6) + jl;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + (size_t)P * N * W * 4);
+  const int w = threadIdx.x & (W - 1), jl = (threadIdx.x >> WL) & 1, k = (threadIdx.x >> (WL + 1)) & 3,
+            j = 2 * (threadIdx.x >> (WL + 3)) + jl;
   const bool live = k < K;
-  const unsigned bytes_t = (unsigned)(K * N * 8 * 8), bytes_p = (unsigned)(P * N * 8 * 4);
+  const unsigned bytes_t = (unsigned)(K * N * W * 8), bytes_p = (unsigned)(P * N * W * 4);
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -59,17 +61,17 @@ __global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constan
   __syncthreads();
   int tile = blockIdx.x;
   if (threadIdx.x == 0 && tile < ntiles) {
-    const int sc = tile / ntz, z0 = (tile - sc * ntz) * 8;
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
     mbar_expect_tx(&bars[0], bytes_t);
     tma_load_3d(st, &tm_t, &bars[0], z0, 0, sc * K);
     mbar_expect_tx(&bars[1], bytes_p);
     tma_load_3d(ps, &tm_psi, &bars[1], z0, 0, 0);
   }
   unsigned ph_t = 0, ph_p = 0;
-  float2* exl = ex + (k * 8 + w) * LS;
+  float2* exl = ex + (k * W + w) * LS;
   for (; tile < ntiles; tile += gridDim.x) {
     const int nxt = tile + gridDim.x;
-    const int sc = tile / ntz, z0 = (tile - sc * ntz) * 8;
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
     bool ok = mbar_wait_bounded(&bars[0], ph_t);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {  // record, then give copies in flight one more bounded wait
@@ -82,17 +84,17 @@ __global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constan
     ph_t ^= 1;
     // forward stage A: DFT_R1 of x[j + 16 q]
     if (live) {
-      const float2* sp = st + (k * N) * 8 + w;
+      const float2* sp = st + (k * N) * W + w;
       float2 a[R1];
 #pragma unroll
-      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * 8];
+      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * W];
       dft_r<R1, false>(a);
 #pragma unroll
       for (int q = 0; q < R1; ++q) exl[j * SF + q] = a[q];
     }
     __syncthreads();
     if (threadIdx.x == 0 && nxt < ntiles) {  // the t block is consumed: fetch the next one
-      const int sn = nxt / ntz, zn = (nxt - sn * ntz) * 8;
+      const int sn = nxt / ntz, zn = (nxt - sn * ntz) * W;
       fence_proxy_async_smem();
       mbar_expect_tx(&bars[0], bytes_t);
       tma_load_3d(st, &tm_t, &bars[0], zn, 0, sn * K);
@@ -119,15 +121,15 @@ __global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constan
     }
     ph_p ^= 1;
     // space-time kernel at the points (ky, c0 .. c0 + 3) of the tile
-    for (int pg = threadIdx.x; pg < 2 * N; pg += blockDim.x) {
-      const int c0 = (pg & 1) * 4, ky = pg >> 1;
+    for (int pg = threadIdx.x; pg < (W / 4) * N; pg += blockDim.x) {
+      const int c0 = (W == 8) ? (pg & 1) * 4 : 0, ky = (W == 8) ? pg >> 1 : pg;
       const int pos = (ky / R1) * SF + (ky % R1);
       float2 v[4][4], u[4][4];
 #pragma unroll
       for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          v[l][c] = (l < K) ? ex[(l * 8 + c0 + c) * LS + pos] : make_float2(0.f, 0.f);
+          v[l][c] = (l < K) ? ex[(l * W + c0 + c) * LS + pos] : make_float2(0.f, 0.f);
           u[l][c] = make_float2(0.f, 0.f);
         }
       int pp = 0;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constan
 #pragma unroll
         for (int b_ = a_; b_ < 4; ++b_)
           if (b_ < K) {
-            const float4 q4 = *reinterpret_cast<const float4*>(ps + (pp * N + ky) * 8 + c0);
+            const float4 q4 = *reinterpret_cast<const float4*>(ps + (pp * N + ky) * W + c0);
             const float pv[4] = {q4.x, q4.y, q4.z, q4.w};
             ++pp;
 #pragma unroll
@@ -153,11 +155,11 @@ __global__ void __launch_bounds__(512, 1) k_col_tma(Geom g, const __grid_constan
       for (int l = 0; l < 4; ++l)
         if (l < K)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) ex[(l * 8 + c0 + c) * LS + pos] = u[l][c];
+          for (int c = 0; c < 4; ++c) ex[(l * W + c0 + c) * LS + pos] = u[l][c];
     }
     __syncthreads();
     if (threadIdx.x == 0 && nxt < ntiles) {  // the Psi block is consumed: fetch the next one
-      const int zn = (nxt - (nxt / ntz) * ntz) * 8;
+      const int zn = (nxt - (nxt / ntz) * ntz) * W;
       fence_proxy_async_smem();
       mbar_expect_tx(&bars[1], bytes_p);
       tma_load_3d(ps, &tm_psi, &bars[1], zn, 0, 0);
@@ -205,22 +207,22 @@ TmaEncodeFn tma_encode_fn() {
 }
 
 namespace {
-template <int N>
+template <int N, int W>
 cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
-  using CT = ColTma<N>;
+  using CT = ColTma<N, W>;
   TmaEncodeFn enc = tma_encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tm_t, tm_psi;
   const cuuint64_t dt[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.S * g.C * g.K};
   const cuuint64_t st_t[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)N * g.nz * 8};
-  const cuuint32_t bt[3] = {8, (cuuint32_t)N, (cuuint32_t)g.K};
+  const cuuint32_t bt[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)g.K};
   const cuuint32_t es[3] = {1, 1, 1};
   if (enc(&tm_t, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, t, dt, st_t, bt, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorNotSupported;
   const cuuint64_t dp[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.P};
   const cuuint64_t sp[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)N * g.nz * 4};
-  const cuuint32_t bp[3] = {8, (cuuint32_t)N, (cuuint32_t)g.P};
+  const cuuint32_t bp[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)g.P};
   if (enc(&tm_psi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(psi), dp, sp, bp, es,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -228,34 +230,39 @@ cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2
   const size_t sm = CT::smem(g.P);
   static int nsm = 0;
   if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::smem(10));
+    cudaError_t e = cudaFuncSetAttribute(k_col_tma<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::smem(10));
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   }
-  const int ntz = g.nz / 8;
+  const int ntz = g.nz / W;
   const long long ntiles = (long long)g.S * g.C * ntz;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>(ntiles, nsm);
-  k_col_tma<N><<<grid, 512, sm, st>>>(g, tm_t, tm_psi, tw, t, ntz, (int)ntiles);
+  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * (8 / W));
+  k_col_tma<N, W><<<grid, 64 * W, sm, st>>>(g, tm_t, tm_psi, tw, t, ntz, (int)ntiles);
   return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t col_tma_w(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
+  if (g.K > 4 || g.nz % W != 0) return cudaErrorNotSupported;
+  switch (g.ny) {
+    case 48: return col_tma_go<48, W>(g, tw_y, psi, t, st);
+    case 64: return col_tma_go<64, W>(g, tw_y, psi, t, st);
+    case 96: return col_tma_go<96, W>(g, tw_y, psi, t, st);
+    case 128: return col_tma_go<128, W>(g, tw_y, psi, t, st);
+    case 160: return col_tma_go<160, W>(g, tw_y, psi, t, st);
+    case 192: return col_tma_go<192, W>(g, tw_y, psi, t, st);
+    case 240: return col_tma_go<240, W>(g, tw_y, psi, t, st);
+    case 256: return col_tma_go<256, W>(g, tw_y, psi, t, st);
+    default: return cudaErrorNotSupported;
+  }
 }
 }  // namespace
 
 cudaError_t launch_col_normal_tma(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
-  if (g.K > 4 || g.nz % 8 != 0) return cudaErrorNotSupported;
-  switch (g.ny) {
-    case 48: return col_tma_go<48>(g, tw_y, psi, t, st);
-    case 64: return col_tma_go<64>(g, tw_y, psi, t, st);
-    case 96: return col_tma_go<96>(g, tw_y, psi, t, st);
-    case 128: return col_tma_go<128>(g, tw_y, psi, t, st);
-    case 160: return col_tma_go<160>(g, tw_y, psi, t, st);
-    case 192: return col_tma_go<192>(g, tw_y, psi, t, st);
-    case 240: return col_tma_go<240>(g, tw_y, psi, t, st);
-    case 256: return col_tma_go<256>(g, tw_y, psi, t, st);
-    default: return cudaErrorNotSupported;
-  }
+  return g.colvar == 4 ? col_tma_w<4>(g, tw_y, psi, t, st) : col_tma_w<8>(g, tw_y, psi, t, st);
 }
 
 }  // namespace t2sh

@@ -454,7 +454,7 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
         const cudaError_t ec = launch_col_normal_tc(g, tw_y, psi, tout, st);
         if (ec != cudaErrorNotSupported) return ec;
       }
-      if (g.colvar == 0 || g.colvar == 3) {
+      if (g.colvar == 0 || g.colvar == 3 || g.colvar == 4) {
         const cudaError_t et = launch_col_normal_tma(g, tw_y, psi, tout, st);
         if (et != cudaErrorNotSupported) return et;
       }

@@ -428,7 +428,7 @@ t2sh_status t2sh_timing_read(t2sh_plan_t p, int32_t cls, int64_t* launches, doub
 
 t2sh_status t2sh_configure(t2sh_plan_t p, int32_t col_variant, int32_t fused_rows) {
   T2SH_REQ(p, "NULL plan");
-  T2SH_REQ(col_variant >= 0 && col_variant <= 3, "col_variant must be 0, 1, 2 or 3");
+  T2SH_REQ(col_variant >= 0 && col_variant <= 4, "col_variant must be in [0, 4]");
   T2SH_REQ(!p->begun || p->iter_done == p->d.iters, "configure must not interrupt a solve in progress");
   p->g.colvar = col_variant;
   p->fused_rows = fused_rows != 0;
@@ -742,7 +742,7 @@ void tune_load() {
                      &a[8]) == 9) {
     char b[128];
     snprintf(b, sizeof(b), "%d %d %d %d %d %d %d", a[0], a[1], a[2], a[3], a[4], a[5], a[6]);
-    if (a[7] >= 0 && a[7] <= 3) g_tune[b] = {a[7], a[8]};
+    if (a[7] >= 0 && a[7] <= 4) g_tune[b] = {a[7], a[8]};
   }
   std::fclose(fp);
 }
@@ -791,7 +791,7 @@ extern "C" t2sh_status t2sh_autotune(t2sh_plan_t p, int32_t probe_iters, int32_t
   int bw = 0, bf = 0;
   t2sh_status st = T2SH_OK;
   // the mixed-precision column pass is the precision's choice, not a tuning candidate
-  const std::vector<int> cols = d.precision == T2SH_MIXED_BF16 ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
+  const std::vector<int> cols = d.precision == T2SH_MIXED_BF16 ? std::vector<int>{3} : std::vector<int>{0, 4, 1, 2};
   for (int colw : cols) {
     for (int fused = 0; fused <= (band_fused_supported(p->g, d.block) ? 1 : 0); ++fused) {
       p->g.colvar = colw;

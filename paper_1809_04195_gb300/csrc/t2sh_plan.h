@@ -35,7 +35,8 @@ struct Geom {
   float inv_sqrt_n;    // 1 / sqrt(ny nz)
   int colvar;          // normal-operator column pass: 0 TMA tiles of 8 columns, 1 cp.async
                        // tiles of 8, 2 cp.async tiles of 4 (size-specialised kernels),
-                       // 3 tensor-core DFT-as-GEMM in split BF16 (mixed precision)
+                       // 3 tensor-core DFT-as-GEMM in split BF16 (mixed precision),
+                       // 4 TMA tiles of 4 columns (two CTAs per SM)
   int* err;            // nullable device flag: set to 1 when a bounded wait ran out
 };
 

@@ -290,15 +290,15 @@ class Plan:
         return (out, res) if residual else out
 
     def autotune(self, probe_iters: int = 3):
-        """(column-pass variant 0 TMA / 1 cp.async x8 / 2 cp.async x4 / 3 tensor cores in
-        split BF16 for MIXED_BF16 plans, fused rows) chosen for this plan's shape."""
+        """(column-pass variant 0 TMA x8 / 4 TMA x4 / 1 cp.async x8 / 2 cp.async x4 / 3 tensor
+        cores in split BF16 for MIXED_BF16 plans, fused rows) chosen for this plan's shape."""
         w, f = ctypes.c_int32(0), ctypes.c_int32(0)
         _check(lib().t2sh_autotune(self._h, int(probe_iters), ctypes.byref(w), ctypes.byref(f)))
         return int(w.value), bool(f.value)
 
     def configure(self, col_variant: int, fused_rows: bool = False):
-        """Pin the column-pass variant (0 TMA, 1 cp.async x8, 2 cp.async x4, 3 tensor cores
-        in split BF16) and row fusion."""
+        """Pin the column-pass variant (0 TMA x8, 4 TMA x4, 1 cp.async x8, 2 cp.async x4,
+        3 tensor cores in split BF16) and row fusion."""
         _check(lib().t2sh_configure(self._h, int(col_variant), 1 if fused_rows else 0))
 
     def sync(self):
