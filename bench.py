@@ -46,22 +46,26 @@ def parse():
                     help="per-slice: one plan and one solve per slice (the plain per-slice form)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["knee", "paper"], default="knee",
+                    help="paper: the Table I scan (288 slices of 260x240, C=7, M=2, b=12, 250 iterations)")
     return ap.parse_args()
 
 
 def workload(args):
     import t2sh_synth as synth
-    sh = synth.KNEE_320x256x160
+    sh = synth.PAPER_288x260x240 if getattr(args, "workload", "knee") == "paper" else synth.KNEE_320x256x160
     S = args.slices or sh.nslices
     iters = args.iters if args.iters is not None else sh.iters
     return sh, S, iters
 
 
 def config_dict(sh, S, iters, n):
-    return {"workload": f"synthetic knee scan, {S} slices of {sh.ny}x{sh.nz}, C={sh.ncoils}, T={sh.nechoes}, "
-                        f"K={sh.nbasis}, {int(sh.frac * 100)}%/echo, b={sh.block}, lambda={sh.lam}, "
-                        f"{iters} FISTA iterations, fp32",
+    kind = "paper-shape (Table I)" if sh.nmaps > 1 else "knee"
+    return {"workload": f"synthetic {kind} scan, {S} slices of {sh.ny}x{sh.nz}, C={sh.ncoils}, T={sh.nechoes}, "
+                        f"K={sh.nbasis}, M={sh.nmaps}, {sh.frac * 100:.3g}%/echo, b={sh.block}, lambda={sh.lam}, "
+                        f"{iters} FISTA iterations",
             "slices": S, "ny": sh.ny, "nz": sh.nz, "coils": sh.ncoils, "echoes": sh.nechoes, "basis": sh.nbasis,
+            "maps": sh.nmaps,
             "iterations": iters, "block": sh.block, "lambda": sh.lam, "parallelism": f"slices, dp{n}",
             "l2": "inputs larger than L2 (per-iteration working set > 6 GB)"}
 
@@ -83,8 +87,9 @@ def oracle_sample(sh, iters):
 def cpu_baseline(sh):
     """Oracle timing in a child process pinned to one BLAS thread."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    name = "PAPER_288x260x240" if sh.nmaps > 1 else "KNEE_320x256x160"
     code = ("import sys, json; sys.path.insert(0, %r); import bench, t2sh_synth as s; "
-            "t, n = bench.oracle_sample(s.KNEE_320x256x160, 30); print(json.dumps([t, n]))") % ROOT
+            "t, n = bench.oracle_sample(s.%s, 30); print(json.dumps([t, n]))") % (ROOT, name)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
@@ -235,14 +240,14 @@ def run_ours(args):
     sh, S, iters = workload(args)
     from paper_1809_04195_gb300.workload import make_scan
     phi_d, mask_d, maps_d, ytil_d = make_scan(sh, S, dev)
-    out_d = torch.empty((S, 1, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    out_d = torch.empty((S, sh.nmaps, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
     prec = t2sh.MIXED_BF16 if args.precision == "mixed" else t2sh.FP32
-    dims = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, block=sh.block,
+    dims = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=sh.nmaps, block=sh.block,
                           lam=sh.lam, iters=iters, seed=sh.seed, precision=prec)
     N = sh.ny * sh.nz
     units = S * iters
 
-    dims1 = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=1, block=sh.block,
+    dims1 = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=1, nmaps=sh.nmaps, block=sh.block,
                            lam=sh.lam, iters=iters, seed=sh.seed, precision=prec)
 
     def step(timing):
@@ -300,7 +305,7 @@ def run_ours(args):
         hmaps = maps_d.cpu().pin_memory()
         hy = ytil_d.cpu().pin_memory()
         hout = torch.empty(out_d.shape, dtype=torch.complex64).pin_memory()
-        hd = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, block=sh.block,
+        hd = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=sh.nmaps, block=sh.block,
                             lam=sh.lam, iters=iters, seed=sh.seed, precision=prec, flags=t2sh.HOST_IO)
 
         def hstep():
@@ -329,7 +334,7 @@ def run_ours(args):
         return
 
     peaks, src = measured_peaks()
-    ab = algorithmic_bytes(1 if args.form == "per-slice" else S, sh.ncoils, 1, sh.nbasis, N)
+    ab = algorithmic_bytes(1 if args.form == "per-slice" else S, sh.ncoils, sh.nmaps, sh.nbasis, N)
     kern = {k: {"launches": n, "ms_total": m, "ms_per_launch": (m / n if n else None),
                 "algorithmic_bytes_per_launch": ab.get(k)} for k, (n, m) in totals.items() if n}
     dom = max((k for k in kern if k in ab), key=lambda k: kern[k]["ms_total"])

@@ -77,8 +77,8 @@ enum {
                                 default: measured slower than the separate kernels        */
 
 typedef struct {
-  int32_t ny, nz;          /* slice matrix (phase encodes y, z); both even, 2/3/5-smooth,
-                              8 <= ny, nz <= 512                                          */
+  int32_t ny, nz;          /* slice matrix (phase encodes y, z); both even, products of
+                              2, 3, 5 and 13 (Table I: 260 x 240), 8 <= ny, nz <= 512     */
   int32_t ncoils;          /* C >= 1 (virtual coils after compression, Sec. III.A)       */
   int32_t nmaps;           /* M in {1, 2}: soft-SENSE map sets (Sec. II.A)               */
   int32_t nechoes;         /* T >= K: echo train length                                  */

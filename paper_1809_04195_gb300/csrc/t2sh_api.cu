@@ -59,13 +59,14 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return zz ^ (zz >> 31);
 }
 
-bool smooth235(int n) {
-  for (int p : {2, 3, 5})
+// sizes the FFT passes cover: products of 2, 3, 5 and 13 (the paper's 260 = 4 * 5 * 13)
+bool smooth_ok(int n) {
+  for (int p : {2, 3, 5, 13})
     while (n % p == 0) n /= p;
   return n == 1;
 }
 
-// Radix plan: as many radix-16 passes as divide n, then 8, 4, 2, 5, 3.
+// Radix plan: as many radix-16 passes as divide n, then 8, 4, 2, 5, 3, 13.
 bool make_fft_plan(int n, FftPlan& p) {
   p.n = n;
   p.npass = 0;
@@ -81,7 +82,7 @@ bool make_fft_plan(int n, FftPlan& p) {
   };
   while (m % 16 == 0)
     if (!add(16)) return false;
-  for (int r : {8, 4, 2, 5, 3})
+  for (int r : {8, 4, 2, 5, 3, 13})
     while (m % r == 0)
       if (!add(r)) return false;
   return m == 1;
@@ -115,7 +116,7 @@ t2sh_status validate(const t2sh_dims* d) {
   T2SH_REQ(d->ny >= 8 && d->nz >= 8 && d->ny <= 512 && d->nz <= 512, "ny, nz must be in [8, 512] (got %d, %d)",
            d->ny, d->nz);
   T2SH_REQ(d->ny % 2 == 0 && d->nz % 2 == 0, "ny, nz must be even (centred FFT)");
-  T2SH_REQ(smooth235(d->ny) && smooth235(d->nz), "ny, nz must be 2/3/5-smooth");
+  T2SH_REQ(smooth_ok(d->ny) && smooth_ok(d->nz), "ny, nz must be products of 2, 3, 5 and 13");
   T2SH_REQ(d->ncoils >= 1 && d->ncoils <= 1024, "ncoils out of range");
   T2SH_REQ(d->nmaps >= 1 && d->nmaps <= kMaxM, "nmaps must be 1 or 2");
   T2SH_REQ(d->nbasis >= 1 && d->nbasis <= kMaxK, "nbasis must be in [1, 8]");

@@ -147,6 +147,48 @@ __device__ __forceinline__ void dft16(float2* v) {
 // n = (B n1 + A n2) mod AB and output map k = (B eA k1 + A eB k2) mod AB, where
 // eA = B^-1 mod A and eB = A^-1 mod B, the length-AB DFT is a 2D A x B DFT with no
 // twiddle factors.  Every index is a compile-time constant.
+// 13-point DFT through the pair symmetry of the kernel: with u_n = x_n + x_(13-n) and
+// w_n = x_n - x_(13-n) (n = 1..6), X_k = x_0 + sum_n cos(2 pi n k / 13) u_n -+ i sum_n
+// sin(2 pi n k / 13) w_n and X_(13-k) the same with the other sign (k = 1..6).  The
+// cosines and sines of 2 pi m / 13 are written out; the index n k mod 13 folds onto
+// m <= 6 at compile time.
+template <bool INV>
+__device__ __forceinline__ void dft13(float2* v) {
+  constexpr float C[7] = {1.0f, 0.88545602565320991f, 0.56806474673115592f, 0.12053668025532301f,
+                          -0.35460488704253545f, -0.74851074817110119f, -0.97094181742605201f};
+  constexpr float S[7] = {0.0f, 0.46472317204376851f, 0.82298386589365635f, 0.99270887409805397f,
+                          0.93501624268541483f, 0.66312265824079519f, 0.23931566428755768f};
+  float2 u[6], w[6];
+#pragma unroll
+  for (int n = 1; n <= 6; ++n) {
+    u[n - 1] = cadd(v[n], v[13 - n]);
+    w[n - 1] = csub(v[n], v[13 - n]);
+  }
+  const float2 x0 = v[0];
+  float2 sum = x0;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) sum = cadd(sum, u[n]);
+  v[0] = sum;
+#pragma unroll
+  for (int k = 1; k <= 6; ++k) {
+    float2 a = x0, b = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n = 1; n <= 6; ++n) {
+      const int m = (n * k) % 13;
+      const float cc = m <= 6 ? C[m] : C[13 - m];
+      const float ss = m <= 6 ? S[m] : -S[13 - m];
+      a.x = fmaf(cc, u[n - 1].x, a.x);
+      a.y = fmaf(cc, u[n - 1].y, a.y);
+      b.x = fmaf(ss, w[n - 1].x, b.x);
+      b.y = fmaf(ss, w[n - 1].y, b.y);
+    }
+    // forward: X_k = a - i b, X_(13-k) = a + i b; inverse the other way round
+    const float2 mib = make_float2(b.y, -b.x), pib = make_float2(-b.y, b.x);
+    v[k] = cadd(a, INV ? pib : mib);
+    v[13 - k] = cadd(a, INV ? mib : pib);
+  }
+}
+
 constexpr int inv_mod(int a, int m) {
   for (int x = 1; x < m; ++x)
     if ((a * x) % m == 1) return x;
@@ -188,6 +230,7 @@ __device__ __forceinline__ void dft_r(float2* v) {
   else if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 10) dft_pfa<2, 5, INV>(v);
   else if constexpr (R == 12) dft_pfa<4, 3, INV>(v);
+  else if constexpr (R == 13) dft13<INV>(v);
   else if constexpr (R == 15) dft_pfa<3, 5, INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
   else static_assert(R == 2, "unsupported radix");
@@ -202,7 +245,7 @@ __device__ __forceinline__ void dft_r(float2* v) {
 // the twiddle read is a broadcast.  Requires nbatch * p.n <= kStage * blockDim.x.
 //   tw[m] = exp(-2 pi i m / n), m < n (shared memory copy).
 // ---------------------------------------------------------------------------------
-constexpr int kStageRegs = 20;  // >= ceil(kStage / R) * R for every radix used
+constexpr int kStageRegs = 26;  // >= ceil(kStage / R) * R for every radix used (13: 2 x 13)
 constexpr int kStageBf = 8;     // >= ceil(kStage / R) for every radix used
 
 template <int R, bool INV>
@@ -257,6 +300,7 @@ __device__ __forceinline__ void fft_lines(float2* buf, int ld, int nbatch, const
       case 2: stockham_pass<2, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
       case 3: stockham_pass<3, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
       case 5: stockham_pass<5, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 13: stockham_pass<13, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
       default: break;
     }
   }

@@ -9,8 +9,9 @@ from __future__ import annotations
 
 
 def make_scan(sh, S: int, dev):
-    """Device-resident synthetic scan: phi, mask, maps [S][C][1][ny][nz], projected k-space
-    ytil [S][C][K][ny][nz] = Phi^T P (F S Phi alpha_true + w), scaled to max |ytil| = 1."""
+    """Device-resident synthetic scan: phi, mask, maps [S][C][M][ny][nz], projected k-space
+    ytil [S][C][K][ny][nz] = Phi^T P (F S Phi alpha_true + w), scaled to max |ytil| = 1
+    (alpha_true in the first map set, zero in the others)."""
     import numpy as np
     import torch
 
@@ -20,22 +21,23 @@ def make_scan(sh, S: int, dev):
     phi, mask, te = synth.scan_common(sh)
     vol = synth.EllipsoidVolume.draw(synth.rng_for(sh.seed, 4, 0))
     N = sh.ny * sh.nz
-    maps = torch.empty((S, sh.ncoils, 1, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
-    alpha = torch.empty((S, 1, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    M = sh.nmaps
+    maps = torch.empty((S, sh.ncoils, M, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
+    alpha = torch.zeros((S, M, sh.nbasis, sh.ny, sh.nz), dtype=torch.complex64, device=dev)
     for s in range(S):
         st = synth.slice_structure(sh, s, volume=vol)
         xt = synth.decay_series(st.rho, st.t2, te)
         a = np.einsum("tk,tyz->kyz", phi, xt)
         maps[s] = torch.from_numpy(st.maps.astype(np.complex64)).to(dev)
-        alpha[s, 0] = torch.from_numpy(a.astype(np.complex64)).to(dev)
+        alpha[s, 0] = torch.from_numpy(a.astype(np.complex64)).to(dev)  # image in the first map set
     phi_d = torch.from_numpy(phi.astype(np.float32)).to(dev)
     mask_d = torch.from_numpy(mask).to(dev)
-    d = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S)
+    d = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=M)
     with t2sh.Plan(d, phi_d, mask_d, maps) as p:
         ytil = p.forward(alpha, t2sh.KSPACE_PROJ)
     # sigma = 1 % of the largest echo-0 sample of the central slice
     c = min(S - 1, S // 2)
-    d1 = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=1)
+    d1 = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=1, nmaps=M)
     with t2sh.Plan(d1, phi_d, mask_d, maps[c:c + 1].contiguous()) as p:
         sig = 0.01 * float(p.forward(alpha[c:c + 1].contiguous(), t2sh.KSPACE_TE)[:, :, 0].abs().max())
     # projected noise Phi^T P w, w ~ CN(0, sigma^2) per echo, drawn echo by echo

@@ -199,6 +199,12 @@ SINGLE_SLICE_64x48 = ScanShape("single slice 64x48, C=8, T=32, K=4, 10%/echo, 50
                                1, 64, 48, 8, 32, 4, 0.10, 0.01, 50, seed=1809)
 KNEE_320x256x160 = ScanShape("knee scan 320 slices of 256x160, C=12, T=80, K=4, 5%/echo, 100 iterations",
                              320, 256, 160, 12, 80, 4, 0.05, 0.005, 100, seed=1810)
+# Table I: 288 readout slices of 260 x 240, C = 7 virtual coils, T = 80, K = 4, M = 2
+# soft-SENSE map sets, 12 x 12 LLR blocks, lambda = 0.0125, 250 FISTA iterations; each echo
+# undersampled by 139 (Sec. V)
+PAPER_288x260x240 = ScanShape("paper scan (Table I) 288 slices of 260x240, C=7, T=80, K=4, M=2, b=12, "
+                              "1/139 per echo, 250 iterations",
+                              288, 260, 240, 7, 80, 4, 1.0 / 139.0, 0.0125, 250, block=12, nmaps=2, seed=1815)
 BATCH_SCANS = (
     KNEE_320x256x160,
     ScanShape("scan 288 slices of 240x128, C=8", 288, 240, 128, 8, 80, 4, 0.05, 0.005, 100, seed=1812),

@@ -50,7 +50,8 @@ def test_workspace_bytes_formula(lib):
 
 @pytest.mark.parametrize("kw,status", [
     (dict(ny=63), t2sh.EINVAL),          # odd
-    (dict(nz=14 * 7), t2sh.EINVAL),      # 98 = 2 * 7^2 is not 2/3/5-smooth
+    (dict(nz=14 * 7), t2sh.EINVAL),      # 98 = 2 * 7^2: 7 is not a radix of the FFT passes
+    (dict(ny=2 * 11 * 5), t2sh.EINVAL),  # 110: 11 neither
     (dict(ny=4), t2sh.EINVAL),           # too small
     (dict(nbasis=9), t2sh.EINVAL),
     (dict(nmaps=3), t2sh.EINVAL),
@@ -67,6 +68,14 @@ def test_invalid_dims_rejected(lib, kw, status):
     n = ctypes.c_size_t(0)
     assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == status
     assert len(t2sh.last_error()) > 0
+
+
+def test_paper_slice_matrix_accepted(lib):
+    """Table I: 260 x 240 slices (260 = 4 * 5 * 13), C = 7, M = 2, b = 12."""
+    d = t2sh.make_dims(260, 240, 7, 80, 4, nslices=288, nmaps=2, block=12, iters=250, lam=0.0125)
+    n = ctypes.c_size_t(0)
+    assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == t2sh.OK
+    assert n.value > 0
 
 
 def test_mixed_precision_dims_accepted(lib):

@@ -86,6 +86,7 @@ SHAPES = [
     (1, 240, 128, 3, 12, 4, 1),  # size-specialised passes with 4-row bands
     (1, 192, 192, 2, 12, 4, 2),  # two map sets on the specialised passes
     (2, 96, 64, 2, 8, 2, 1),     # K = 2 on the specialised passes
+    (1, 260, 240, 7, 16, 4, 2),  # Table I slice matrix: radix-13 passes, C = 7, M = 2
 ]
 
 
@@ -140,6 +141,7 @@ def test_step_matches_oracle(T):
     (40, 24, 6, 5, 0, 2, 4),    # two map sets
     (48, 30, 8, 1, 6, 1, 6),    # K > 4
     (256, 160, 8, 0, 0, 1, 4),
+    (260, 240, 12, 7, 11, 2, 4),  # Table I: 12 x 12 blocks, 260 mod 12 = 8, two map sets
 ])
 def test_llr_prox_matches_oracle(T, ny, nz, b, sy, sz, M, K):
     rng, phi, mask, maps = random_problem(ny * nz + b, 2, ny, nz, 2, max(K, 8), K, M)
@@ -259,6 +261,25 @@ def test_solve_knee_slices_projected(T):
         ref = O.fista(ys[i], "proj", maps[i], mask, phi, sh.lam, sh.block, sh.iters, sh.seed)
         e = nrmse(got[i], ref)
         print("knee slice", sl[i], "NRMSE", e)
+        assert e < SOLVE_TOL
+
+
+def test_solve_paper_shape_slices(T):
+    """Two slices of the Table I scan (260 x 240, C = 7, T = 80, K = 4, M = 2 soft-SENSE
+    map sets, 12 x 12 LLR blocks, lambda = 0.0125, 1/139 of k-space per echo), projected
+    input, 20 FISTA iterations, against the oracle."""
+    sh = synth.PAPER_288x260x240
+    sl = [0, 144]
+    phi, mask, maps, ytil = proj_scan(sh, sl)
+    phi, maps = r32(phi, maps)
+    it = 20
+    with make_plan(T, phi, mask, maps, block=sh.block, lam=sh.lam, iters=it, seed=sh.seed) as p:
+        got = host(p.solve(c64(ytil), T.KSPACE_PROJ))
+    ys = ytil.astype(np.complex64).astype(np.complex128)
+    for i in range(len(sl)):
+        ref = O.fista(ys[i], "proj", maps[i], mask, phi, sh.lam, sh.block, it, sh.seed)
+        e = nrmse(got[i], ref)
+        print("paper-shape slice", sl[i], "NRMSE", e)
         assert e < SOLVE_TOL
 
 
