@@ -262,6 +262,64 @@ def fista(kspace: np.ndarray, kform: str, maps: np.ndarray, mask: np.ndarray, ph
     return x
 
 
+def cg(apply_op, rhs: np.ndarray, x0: np.ndarray, iters: int) -> np.ndarray:
+    """Conjugate gradients (Hestenes and Stiefel) for the Hermitian positive definite
+    system apply_op(x) = rhs, started at x0, exactly ``iters`` iterations:
+      r = rhs - A x0, p = r;  a = <r, r> / <p, A p>;  x += a p;  r -= a A p;
+      b = <r_new, r_new> / <r, r>;  p = r + b p.
+    A zero denominator makes its quotient zero, so a solved system stays put."""
+    x = x0.astype(np.complex128).copy()
+    r = rhs - apply_op(x)
+    p = r.copy()
+    rr = float(np.vdot(r, r).real)
+    for _ in range(iters):
+        q = apply_op(p)
+        pq = float(np.vdot(p, q).real)
+        a = rr / pq if pq != 0.0 else 0.0
+        x = x + a * p
+        r = r - a * q
+        rr_new = float(np.vdot(r, r).real)
+        bb = rr_new / rr if rr != 0.0 else 0.0
+        p = r + bb * p
+        rr = rr_new
+    return x
+
+
+def admm(kspace: np.ndarray, kform: str, maps: np.ndarray, mask: np.ndarray, phi: np.ndarray,
+         lam: float, b: int, iters: int, seed: int, rho: float, cg_iters: int,
+         shifts: bool = True, return_all: bool = False):
+    """Solve Eq. 5 by ``iters`` iterations of ADMM in scaled form with the splitting
+    alpha = v (the LLR term on v), starting from alpha = v = u = 0:
+      alpha_{k+1} = argmin 1/2 ||A alpha - y||^2 + rho/2 ||alpha - v_k + u_k||^2, i.e.
+                    (A^H A + rho I) alpha = A^H y + rho (v_k - u_k), by ``cg_iters``
+                    conjugate-gradient iterations started at alpha_k;
+      v_{k+1}     = LLR prox of alpha_{k+1} + u_k with threshold lambda / rho and the
+                    shift of iteration k (the same shift sequence as FISTA);
+      u_{k+1}     = u_k + alpha_{k+1} - v_{k+1}.
+    Returns v [M][K][Ny][Nz] (and alpha, u with return_all)."""
+    C, M = maps.shape[:2]
+    K = phi.shape[1]
+    Ny, Nz = mask.shape[1:]
+    psi = space_time_kernel(mask, phi)
+    aty = adjoint_data(kspace, kform, maps, mask, phi)
+    alpha = np.zeros((M, K, Ny, Nz), np.complex128)
+    v = np.zeros_like(alpha)
+    u = np.zeros_like(alpha)
+    sh = llr_shifts(seed, iters, b) if shifts else np.zeros((iters, 2), np.int64)
+
+    def op(x):
+        return normal(x, maps, psi) + rho * x
+
+    for it in range(iters):
+        alpha = cg(op, aty + rho * (v - u), alpha, cg_iters)
+        w = alpha + u
+        v = llr_prox(w, b, lam / rho, int(sh[it, 0]), int(sh[it, 1]))
+        u = w - v
+    if return_all:
+        return v, alpha, u
+    return v
+
+
 def objective(alpha: np.ndarray, y: np.ndarray, maps: np.ndarray, mask: np.ndarray,
               phi: np.ndarray, lam: float, b: int, sy: int = 0, sz: int = 0) -> float:
     """Eq. 5 cost for T-form data y with the block grid of shift (sy, sz)."""

@@ -399,3 +399,76 @@ def test_fista_rate_bound_beck_teboulle():
     for k in (1, 5, 20, 50, 100, 200):
         fk = 0.5 * np.linalg.norm(A @ tr[k - 1].ravel() - y.ravel()) ** 2
         assert fk - fstar <= 2 * L * R2 / (k + 1) ** 2 + 1e-12
+
+
+# ----------------------------------------------------------------------------------
+# ADMM with conjugate-gradient inner solves
+# ----------------------------------------------------------------------------------
+def test_cg_solves_a_dense_hpd_system_in_n_steps():
+    """n CG iterations solve an n x n Hermitian positive definite system (exact
+    arithmetic; float64 to 1e-9), against numpy's dense solver."""
+    rng = np.random.default_rng(5)
+    n = 12
+    B = crandn(rng, n, n)
+    H = B.conj().T @ B + 0.5 * np.eye(n)
+    rhs = crandn(rng, n)
+    x = O.cg(lambda v: H @ v, rhs, np.zeros(n, complex), n)
+    assert np.abs(x - np.linalg.solve(H, rhs)).max() < 1e-9 * np.abs(np.linalg.solve(H, rhs)).max()
+    # a solved system stays put (zero residual: zero step, zero direction)
+    x2 = O.cg(lambda v: H @ v, rhs, np.linalg.solve(H, rhs), 3)
+    assert np.abs(x2 - np.linalg.solve(H, rhs)).max() < 1e-12
+
+
+def test_cg_on_the_regularised_normal_equations_matches_dense_solve():
+    """The ADMM alpha-update (A^H A + rho I) alpha = rhs through the oracle's normal
+    operator equals the dense solve with the Kronecker-built A."""
+    phi, maps, mask, rng = tiny_problem(79, frac=0.4)
+    A = dense_A(maps, mask, phi)
+    psi = O.space_time_kernel(mask, phi)
+    rho = 0.3
+    rhs = crandn(rng, 1, 2, 8, 8)
+    H = A.conj().T @ A + rho * np.eye(A.shape[1])
+    ref = np.linalg.solve(H, rhs.ravel())
+    x = O.cg(lambda v: O.normal(v, maps, psi) + rho * v, rhs, np.zeros_like(rhs), 200)
+    assert np.abs(x.ravel() - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_admm_lambda0_recovers_noiseless_full_sampling():
+    """lambda = 0: the prox is the identity, u stays 0 and the alpha-update is a proximal
+    point step towards the least-squares solution, here the noiseless phantom."""
+    rng = np.random.default_rng(2)
+    T, K, C, ny, nz = 12, 3, 3, 12, 8
+    phi = synth.t2_basis(T, K)
+    maps = synth.coil_maps(C, ny, nz, rng)
+    full = np.ones((T, ny, nz), np.uint8)
+    a_true = crandn(rng, 1, K, ny, nz)
+    y = O.forward(a_true, maps, full, phi)
+    v, alpha, u = O.admm(y, "te", maps, full, phi, lam=0.0, b=4, iters=40, seed=1, rho=0.5, cg_iters=3,
+                         return_all=True)
+    assert np.abs(u).max() < 1e-12
+    assert np.abs(v - a_true).max() < 1e-9 * np.abs(a_true).max()
+
+
+def test_admm_and_fista_reach_the_same_convex_minimiser():
+    """Shifts off: ADMM (exact enough inner solves) and FISTA minimise the same convex
+    Eq. 5 cost; both reach one minimiser and cost, and the ADMM fixed point satisfies
+    v = prox(v - (A^H A v - A^H y) / rho) with threshold lambda / rho, the optimality
+    condition of the cost (u = (A^H y - A^H A v) / rho at the fixed point)."""
+    phi, maps, mask, rng = tiny_problem(80, frac=0.7)
+    A = dense_A(maps, mask, phi)
+    a_true = crandn(rng, 1, 2, 8, 8)
+    y = (A @ a_true.ravel()).reshape(2, 6, 8, 8) + 0.1 * crandn(rng, 2, 6, 8, 8) * mask[None]
+    lam, b, rho = 0.3, 4, 0.5
+    x_f = O.fista(y, "te", maps, mask, phi, lam=lam, b=b, iters=3000, seed=0, shifts=False)
+    v, alpha, u = O.admm(y, "te", maps, mask, phi, lam=lam, b=b, iters=600, seed=0, rho=rho, cg_iters=12,
+                         shifts=False, return_all=True)
+    f_f = O.objective(x_f, y, maps, mask, phi, lam, b)
+    f_a = O.objective(v, y, maps, mask, phi, lam, b)
+    assert abs(f_a - f_f) <= 1e-8 * abs(f_f)
+    assert np.abs(v - x_f).max() < 1e-6
+    assert np.abs(alpha - v).max() < 1e-8  # primal residual
+    psi = O.space_time_kernel(mask, phi)
+    aty = O.adjoint(y, maps, mask, phi)
+    assert np.abs(u - (aty - O.normal(v, maps, psi)) / rho).max() < 1e-7
+    g = v - (O.normal(v, maps, psi) - aty) / rho
+    assert np.abs(O.llr_prox(g, b, lam / rho, 0, 0) - v).max() < 1e-7
