@@ -46,6 +46,10 @@ def parse():
                     help="per-slice: one plan and one solve per slice (the plain per-slice form)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solver", choices=["fista", "admm"], default="fista",
+                    help="admm: t2sh_solve_admm (CG alpha-updates); an iteration is one outer ADMM iteration")
+    ap.add_argument("--rho", type=float, default=0.5)
+    ap.add_argument("--cg-iters", type=int, default=3)
     ap.add_argument("--workload", choices=["knee", "paper"], default="knee",
                     help="paper: the Table I scan (288 slices of 260x240, C=7, M=2, b=12, 250 iterations)")
     return ap.parse_args()
@@ -268,7 +272,10 @@ def run_ours(args):
         p = t2sh.Plan(dims, phi_d, mask_d, maps_d)
         if timing:
             p.timing(True)
-        p.solve(ytil_d, t2sh.KSPACE_PROJ, out=out_d)
+        if args.solver == "admm":
+            p.solve_admm(ytil_d, t2sh.KSPACE_PROJ, rho=args.rho, cg_iters=args.cg_iters, out=out_d)
+        else:
+            p.solve(ytil_d, t2sh.KSPACE_PROJ, out=out_d)
         tm = p.timing_read() if timing else None
         p.close()
         return tm
@@ -310,7 +317,10 @@ def run_ours(args):
 
         def hstep():
             p = t2sh.Plan(hd, hphi, hmask, hmaps)
-            p.solve(hy, t2sh.KSPACE_PROJ, out=hout)
+            if args.solver == "admm":
+                p.solve_admm(hy, t2sh.KSPACE_PROJ, rho=args.rho, cg_iters=args.cg_iters, out=hout)
+            else:
+                p.solve(hy, t2sh.KSPACE_PROJ, out=hout)
             p.close()
 
         hstep()
@@ -335,6 +345,11 @@ def run_ours(args):
 
     peaks, src = measured_peaks()
     ab = algorithmic_bytes(1 if args.form == "per-slice" else S, sh.ncoils, sh.nmaps, sh.nbasis, N)
+    if args.solver == "admm":
+        vec = (1 if args.form == "per-slice" else S) * sh.nmaps * sh.nbasis * N * 8
+        ab["llr"] = 4 * vec  # read alpha, u; write v, u
+        # per outer iteration: init (5 reads, 2 writes) + cg_iters x (dot 2, step 4 + 2, dir 2 + 1)
+        ab["cg"] = (7 + 11 * args.cg_iters) * vec / (1 + 3 * args.cg_iters)
     kern = {k: {"launches": n, "ms_total": m, "ms_per_launch": (m / n if n else None),
                 "algorithmic_bytes_per_launch": ab.get(k)} for k, (n, m) in totals.items() if n}
     dom = max((k for k in kern if k in ab), key=lambda k: kern[k]["ms_total"])
@@ -353,7 +368,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == t2sh.FP32 else "f32 + bf16x3 (column DFTs on tensor cores, f32 accumulate)",
             "data": "synthetic (seeded 3D ellipsoid knee phantom, smooth coil maps, variable-density masks)",
-            "config": {**config_dict(sh, S, iters, world), "precision": args.precision, "form": args.form}, "roofline": roof, "gpu_launches": launches,
+            "config": {**config_dict(sh, S, iters, world), "precision": args.precision, "form": args.form,
+                       **({"solver": f"admm rho={args.rho} cg_iters={args.cg_iters}"} if args.solver == "admm" else {})}, "roofline": roof, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": e2e}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sh)

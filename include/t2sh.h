@@ -169,6 +169,23 @@ t2sh_status t2sh_solve(t2sh_plan_t plan, const void* kspace, int32_t kform, void
                        double* residual_out);
 
 /*
+ * t2sh_solve_admm -- the same problem (Eq. 5, Sec. II.A) solved by ADMM in scaled form
+ * instead of FISTA, with the splitting alpha = v (the LLR term on v) and conjugate-gradient
+ * alpha-updates.  From alpha = v = u = 0, for each of dims.iters iterations k:
+ *   alpha <- cg_iters CG iterations on (A^H A + rho I) alpha = A^H y + rho (v - u), started
+ *            at the previous alpha (per-slice float64 dot products);
+ *   v     <- LLR prox of alpha + u with threshold lambda / rho and shift k (the FISTA
+ *            shift sequence);
+ *   u     <- u + alpha - v.
+ * alpha_out receives v [S][M][K][ny][nz].  rho > 0 (finite), 0 <= cg_iters <= 1000.
+ * residual_out (nullable, dims.iters doubles): ||v_{k+1} - v_k|| / ||v_{k+1}|| per
+ * iteration.  The paper itself uses FISTA; this is the alternative solver loop.  Allocates
+ * three more vectors in the plan on its first call.  Leaves no resumable state.
+ */
+t2sh_status t2sh_solve_admm(t2sh_plan_t plan, const void* kspace, int32_t kform, void* alpha_out, float rho,
+                            int32_t cg_iters, double* residual_out);
+
+/*
  * Resumable solve, for schedulers that interleave several scans (t2sh_solve is
  * t2sh_solve_begin + t2sh_solve_iterate(dims.iters) + t2sh_solve_end):
  *   t2sh_solve_begin    forms A^H y from the k-space (as t2sh_solve) and resets the FISTA
@@ -251,6 +268,7 @@ t2sh_status t2sh_workspace_bytes(const t2sh_dims* dims, size_t* bytes);
  *   4 (reserved: plan-time kernels run inside t2sh_plan, before timing can be enabled)
  *   5 projection of per-echo k-space
  *   6 fused band kernel of t2sh_solve (row adjoint + gradient + LLR + momentum + row forward)
+ *   7 conjugate-gradient vector kernels of t2sh_solve_admm
  * t2sh_timing_enable(plan, 1) clears the counters and starts recording; (plan, 0) stops.
  * t2sh_timing_read synchronises the stream and returns the launch count and the summed
  * event-to-event milliseconds of one class since the last enable.  Recording adds two

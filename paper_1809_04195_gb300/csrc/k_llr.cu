@@ -8,17 +8,24 @@
 // by default, float64 on request), sigma_i = sqrt(lambda_i), and forms
 // W = V diag(max(1 - tau/sigma_i, 0)) V^H,
 // so that X W = U max(Sigma - tau, 0) V^H (since X V = U Sigma).  The FISTA variant
-// fuses the gradient step before the prox and the momentum update after it (Sec. II.A).
+// fuses the gradient step before the prox and the momentum update after it (Sec. II.A);
+// the ADMM variant thresholds alpha + u and writes v and the scaled dual u + alpha - v.
 #include "t2sh_device.cuh"
 
 namespace t2sh {
 
+enum { LLR_PROX = 0, LLR_FISTA = 1, LLR_ADMM = 2 };
+
 // The K <= 4 float32 variant is held to 80 registers so that three CTAs share an SM and
 // the single-thread eigen-steps of one band overlap the memory phases of the others.
-template <int KC, bool FISTA, typename ET>
+// MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
+// z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
+// u <- w - v.
+template <int KC, int MODE, typename ET>
 __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1)
-    k_llr(Geom g, FistaArgs a, float2* x, float2* z,
-                                                const float2* __restrict__ grad, const float2* __restrict__ aty) {
+    k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
+          const float2* __restrict__ aty, float2* u) {
+  constexpr bool FISTA = MODE == LLR_FISTA;
   extern __shared__ float2 smem[];
   const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, M = g.M, b = a.b;
   const int s = blockIdx.y, band = blockIdx.x;
@@ -41,7 +48,11 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
     const int y = (a.sy + band * b + r) % ny;
     const long long gi = ((long long)s * M * K + rest) * N + (long long)y * nz + zz;
     float4 v;
-    if (FISTA) {
+    if (MODE == LLR_ADMM) {
+      const float4 av = *reinterpret_cast<const float4*>(x + gi);
+      const float4 uv = *reinterpret_cast<const float4*>(u + gi);
+      v = make_float4(av.x + uv.x, av.y + uv.y, av.z + uv.z, av.w + uv.w);
+    } else if (FISTA) {
       const float4 zv = *reinterpret_cast<const float4*>(z + gi);
       const float4 gv = *reinterpret_cast<const float4*>(grad + gi);
       const float4 av = *reinterpret_cast<const float4*>(aty + gi);
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
   // 4. X' = X W, then FISTA momentum; write back.  The optional convergence monitor sums
   // |x_{k+1} - x_k|^2 and |x_{k+1}|^2 in float32 per thread (float64 only for the
   // cross-thread reduction: the float64 pipe is a small fraction of float32 on GB300).
-  const bool want_res = FISTA && a.res != nullptr;
+  const bool want_res = (FISTA || MODE == LLR_ADMM) && a.res != nullptr;
   float d2 = 0.f, x2 = 0.f;
   const int npx = M * rb * nz;
   for (int e = threadIdx.x; e < npx; e += kThreads) {
@@ -124,6 +135,16 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
 #pragma unroll
         for (int l = 0; l < KC; ++l) cfma(o, xv[l], w[l * KC + k]);
         const long long gi = gb + (long long)k * N;
+        if (MODE == LLR_ADMM) {
+          if (want_res) {
+            const float2 dv = csub(o, z[gi]);
+            d2 = fmaf(dv.x, dv.x, fmaf(dv.y, dv.y, d2));
+            x2 = fmaf(o.x, o.x, fmaf(o.y, o.y, x2));
+          }
+          z[gi] = o;
+          u[gi] = csub(xv[k], o);
+          continue;
+        }
         if (FISTA) {
           const float2 xo = x[gi];
           const float2 dx = csub(o, xo);
@@ -151,35 +172,43 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
   }
 }
 
-template <int KC, bool FISTA, typename ET>
+template <int KC, int MODE, typename ET>
 static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
-                          const float2* aty, cudaStream_t st) {
+                          const float2* aty, float2* u, cudaStream_t st) {
   const int nbz = (g.nz + a.b - 1) / a.b;
   const int nblk = g.M * nbz;
   const size_t sm = sizeof(float2) * ((size_t)g.M * g.K * a.b * g.nz + (size_t)nblk * KC * KC) +
                     sizeof(float) * (size_t)nblk * KC * KC;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_llr<KC, FISTA, ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_llr<KC, MODE, ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((g.ny + a.b - 1) / a.b, g.S);
-  k_llr<KC, FISTA, ET><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty);
+  k_llr<KC, MODE, ET><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty, u);
   return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t llr_mode(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
+                            const float2* aty, float2* u, cudaStream_t st) {
+  if (a.eig64)
+    return g.K <= 4 ? llr_go<4, MODE, double>(g, a, x, z, grad, aty, u, st)
+                    : llr_go<8, MODE, double>(g, a, x, z, grad, aty, u, st);
+  return g.K <= 4 ? llr_go<4, MODE, float>(g, a, x, z, grad, aty, u, st)
+                  : llr_go<8, MODE, float>(g, a, x, z, grad, aty, u, st);
 }
 
 cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                        const float2* aty, cudaStream_t st) {
-  const bool fista = (z != nullptr);
-  if (a.eig64) {
-    if (g.K <= 4)
-      return fista ? llr_go<4, true, double>(g, a, x, z, grad, aty, st) : llr_go<4, false, double>(g, a, x, z, grad, aty, st);
-    return fista ? llr_go<8, true, double>(g, a, x, z, grad, aty, st) : llr_go<8, false, double>(g, a, x, z, grad, aty, st);
-  }
-  if (g.K <= 4)
-    return fista ? llr_go<4, true, float>(g, a, x, z, grad, aty, st) : llr_go<4, false, float>(g, a, x, z, grad, aty, st);
-  return fista ? llr_go<8, true, float>(g, a, x, z, grad, aty, st) : llr_go<8, false, float>(g, a, x, z, grad, aty, st);
+  return z != nullptr ? llr_mode<LLR_FISTA>(g, a, x, z, grad, aty, nullptr, st)
+                      : llr_mode<LLR_PROX>(g, a, x, nullptr, nullptr, nullptr, nullptr, st);
+}
+
+cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alpha, float2* v, float2* u,
+                            cudaStream_t st) {
+  return llr_mode<LLR_ADMM>(g, a, const_cast<float2*>(alpha), v, nullptr, nullptr, u, st);
 }
 
 size_t llr_smem_bytes(const Geom& g, int b) {

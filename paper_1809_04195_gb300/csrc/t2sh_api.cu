@@ -178,12 +178,18 @@ struct t2sh_plan_s {
   bool record_res = false;
   bool fused_rows = false;  // tunable: fused band kernel for the row work
   // kernel timing (t2sh_timing_*)
-  static constexpr int kClasses = 7;
+  static constexpr int kClasses = 8;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   size_t ev_next = 0;
-  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // ADMM state (allocated on the first t2sh_solve_admm): scaled dual u, CG residual and
+  // direction, per-slice float64 accumulators rr[3][S] and pq[S]
+  float2* u = nullptr;
+  float2* cg_r = nullptr;
+  float2* cg_p = nullptr;
+  double* cg_red = nullptr;
 
   template <typename T>
   t2sh_status alloc(T** p, size_t bytes) {
@@ -235,7 +241,7 @@ struct KTimer {
     }
   }
 };
-enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5, KC_BAND = 6 };
+enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5, KC_BAND = 6, KC_CG = 7 };
 }  // namespace
 
 namespace {
@@ -578,13 +584,13 @@ t2sh_status iterate_impl(t2sh_plan_t p, int n) {
   return T2SH_OK;
 }
 
-t2sh_status end_impl(t2sh_plan_t p, void* alpha_out, double* residual_out) {
+t2sh_status end_impl(t2sh_plan_t p, void* alpha_out, double* residual_out, const float2* src = nullptr) {
   T2SH_REQ(p && alpha_out, "NULL argument");
   T2SH_REQ(p->begun, "t2sh_solve_begin has not been called on this plan");
   const t2sh_dims& d = p->d;
   const size_t vec = footprint(d).vec;
-  T2SH_CK(cudaMemcpyAsync(alpha_out, p->x, vec, p->host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                          p->st));
+  T2SH_CK(cudaMemcpyAsync(alpha_out, src ? src : p->x, vec,
+                          p->host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, p->st));
   if (residual_out && p->iter_done > 0) {
     T2SH_REQ(p->record_res, "the monitor was not recorded for this solve");
     std::vector<double> r(2 * (size_t)p->iter_done);
@@ -607,6 +613,68 @@ t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* a
   t2sh_status s = begin_impl(p, kspace, kform, residual_out != nullptr);
   if (s == T2SH_OK) s = iterate_impl(p, p->d.iters);
   if (s == T2SH_OK) s = end_impl(p, alpha_out, residual_out);
+  return s;
+}
+
+// ADMM (scaled form) for Eq. 5 with conjugate-gradient alpha-updates; the iteration the
+// oracle's admm() states step by step.  alpha lives in p->x, v in p->z, u in p->u.
+t2sh_status t2sh_solve_admm(t2sh_plan_t p, const void* kspace, int32_t kform, void* alpha_out, float rho,
+                            int32_t cg_iters, double* residual_out) {
+  T2SH_REQ(p && kspace && alpha_out, "NULL argument");
+  T2SH_REQ(std::isfinite(rho) && rho > 0.f, "rho must be finite and > 0");
+  T2SH_REQ(cg_iters >= 0 && cg_iters <= 1000, "cg_iters must be in [0, 1000]");
+  const t2sh_dims& d = p->d;
+  const Geom& g = p->g;
+  const size_t vec = footprint(d).vec;
+  if (!p->u) {
+    t2sh_status a = p->alloc(&p->u, vec);
+    if (a == T2SH_OK) a = p->alloc(&p->cg_r, vec);
+    if (a == T2SH_OK) a = p->alloc(&p->cg_p, vec);
+    if (a == T2SH_OK) a = p->alloc(&p->cg_red, sizeof(double) * 4 * (size_t)d.nslices);
+    if (a != T2SH_OK) return a;
+  }
+  t2sh_status s = begin_impl(p, kspace, kform, residual_out != nullptr);
+  if (s != T2SH_OK) return s;
+  T2SH_CK(cudaMemsetAsync(p->u, 0, vec, p->st));
+  double* rr[3] = {p->cg_red, p->cg_red + d.nslices, p->cg_red + 2 * (size_t)d.nslices};
+  double* pq = p->cg_red + 3 * (size_t)d.nslices;
+  for (int it = 0; it < d.iters; ++it) {
+    if (cg_iters > 0) {
+      // alpha-update: cg_iters CG steps on (A^H A + rho I) alpha = A^H y + rho (v - u) from alpha
+      T2SH_CK(cudaMemsetAsync(p->cg_red, 0, sizeof(double) * 4 * (size_t)d.nslices, p->st));
+      if (it == 0) {
+        T2SH_CK(cudaMemsetAsync(p->grad, 0, vec, p->st));  // alpha_0 = 0
+      } else {
+        s = normal_op(p, p->x, p->grad);
+        if (s != T2SH_OK) return s;
+      }
+      {
+        KTimer k(p, KC_CG);
+        T2SH_CK(launch_cg_init(g, p->x, p->grad, p->aty, p->z, p->u, rho, p->cg_r, p->cg_p, rr[0], p->st));
+      }
+      for (int i = 0; i < cg_iters; ++i) {
+        s = normal_op(p, p->cg_p, p->grad);
+        if (s != T2SH_OK) return s;
+        KTimer k(p, KC_CG);
+        T2SH_CK(launch_cg_dot(g, p->cg_p, p->grad, rho, pq, p->st));
+        T2SH_CK(launch_cg_step(g, p->x, p->cg_r, p->cg_p, p->grad, rho, rr[i % 3], pq, rr[(i + 1) % 3], p->st));
+        T2SH_CK(launch_cg_dir(g, p->cg_r, p->cg_p, rr[i % 3], rr[(i + 1) % 3], pq, rr[(i + 2) % 3], p->st));
+      }
+    }
+    // v-update (LLR prox of alpha + u, threshold lambda / rho, this iteration's shift) and dual update
+    FistaArgs a{};
+    a.tau = d.lambda / rho;
+    a.sy = p->shifts[2 * it];
+    a.sz = p->shifts[2 * it + 1];
+    a.b = d.block;
+    a.eig64 = (d.flags & T2SH_EIG_FP64) ? 1 : 0;
+    a.res = p->record_res ? p->res + 2 * it : nullptr;
+    KTimer k(p, KC_LLR);
+    T2SH_CK(launch_llr_admm(g, a, p->x, p->z, p->u, p->st));
+  }
+  p->iter_done = d.iters;
+  s = end_impl(p, alpha_out, residual_out, p->z);
+  p->begun = false;  // the FISTA state was not kept: no t2sh_solve_iterate on top of this
   return s;
 }
 

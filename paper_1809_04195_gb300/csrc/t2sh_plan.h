@@ -78,6 +78,17 @@ cudaError_t launch_row(const Geom& g, RowMode mode, const FftPlan& pz, const flo
                        const float2* x, float2* t, float2* out, cudaStream_t st);
 cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const float2* tw_y, const float* psi,
                        const float* phi, const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st);
+// ADMM v-update: w = alpha + u, v = LLR prox of w (threshold a.tau, shift a.sy/a.sz), u <- w - v
+cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alpha, float2* v, float2* u,
+                            cudaStream_t st);
+// conjugate-gradient vector kernels of the ADMM alpha-update (per-slice float64 accumulators)
+cudaError_t launch_cg_init(const Geom& g, const float2* x, const float2* w, const float2* aty, const float2* v,
+                           const float2* u, float rho, float2* r, float2* p, double* rr, cudaStream_t st);
+cudaError_t launch_cg_dot(const Geom& g, const float2* p, const float2* w, float rho, double* pq, cudaStream_t st);
+cudaError_t launch_cg_step(const Geom& g, float2* x, float2* r, const float2* p, const float2* w, float rho,
+                           const double* rr, const double* pq, double* rr_new, cudaStream_t st);
+cudaError_t launch_cg_dir(const Geom& g, const float2* r, float2* p, const double* rr, const double* rr_new,
+                          double* pq, double* rr_next, cudaStream_t st);
 cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                        const float2* aty, cudaStream_t st);
 

@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
             "t2sh_normal_op": [_vp, _vp, _vp],
             "t2sh_llr_prox": [_vp, _vp, _f32, _i32, _i32],
             "t2sh_solve": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
+            "t2sh_solve_admm": [_vp, _vp, _i32, _vp, _f32, _i32, ctypes.POINTER(ctypes.c_double)],
             "t2sh_get_step": [_vp, ctypes.POINTER(_f32)],
             "t2sh_shifts": [_u64, _i32, _i32, ctypes.POINTER(_i32)],
             "t2sh_workspace_bytes": [ctypes.POINTER(Dims), ctypes.POINTER(ctypes.c_size_t)],
@@ -263,6 +264,27 @@ class Plan:
         _check(lib().t2sh_solve(self._h, kp, kform, op, rp))
         return (out, res) if residual else out
 
+    def solve_admm(self, kspace, kform=KSPACE_PROJ, rho: float = 1.0, cg_iters: int = 3, out=None,
+                   residual: bool = False):
+        """ADMM solve (CG alpha-updates, LLR prox on v); returns v (and the per-iteration
+        relative change of v if asked)."""
+        import torch
+        if self.host_io:
+            if out is None:
+                out = np.empty(self.vec_shape, np.complex64)
+            kp = _ptr(kspace, torch.complex64, self._kshape(kform), True)
+            op = _ptr(out, torch.complex64, self.vec_shape, True)
+        else:
+            out = self._empty(self.vec_shape) if out is None else out
+            kp, op = self._dev(kspace, self._kshape(kform)), self._dev(out, self.vec_shape)
+        res = None
+        rp = None
+        if residual:
+            res = np.zeros(max(self.dims.iters, 0), np.float64)
+            rp = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().t2sh_solve_admm(self._h, kp, kform, op, float(rho), int(cg_iters), rp))
+        return (out, res) if residual else out
+
     # -- resumable solve (schedulers interleaving scans) --------------------------------
     def solve_begin(self, kspace, kform=KSPACE_PROJ):
         import torch
@@ -307,7 +329,7 @@ class Plan:
         _check(lib().t2sh_sync(self._h))
 
     # -- kernel timing ----------------------------------------------------------------
-    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band"}
+    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band", 7: "cg"}
 
     def timing(self, enable: bool):
         _check(lib().t2sh_timing_enable(self._h, 1 if enable else 0))
