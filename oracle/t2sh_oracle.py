@@ -320,6 +320,48 @@ def admm(kspace: np.ndarray, kform: str, maps: np.ndarray, mask: np.ndarray, phi
     return v
 
 
+def synthesize_te(alpha: np.ndarray, maps: np.ndarray, phi: np.ndarray, te_index) -> np.ndarray:
+    """Virtual-coil images at the listed echoes (Sec. III.C, Process TE): back-projection
+    with the basis, x_m(t) = sum_k Phi[t, k] alpha[m, k], then the coil model
+    x_c(t) = sum_m S_{c,m} x_m(t).  Returns [nte][C][Ny][Nz]."""
+    xt = np.einsum("tk,mkyz->tmyz", phi[np.asarray(te_index)], alpha)
+    return np.einsum("cmyz,tmyz->tcyz", maps, xt)
+
+
+def homodyne_z(x: np.ndarray, pf: float) -> np.ndarray:
+    """Homodyne detection (Noll 1991) along z, the slice direction, for partial Fourier
+    fraction pf in (1/2, 1].  With the centred, unitary DFT along z (frequency d relative
+    to DC at Nz/2), the acquired lines are d in [-w, Nz/2) with w = ceil(pf Nz) - Nz/2;
+    the band |d| <= w is sampled on both sides.  Weighting H(d) = 0 (d < -w), 1 (|d| <= w),
+    2 (d > w); phase from the band alone, phi = arg IFFT(k 1_band);
+    result Re(IFFT(H k) e^(-i phi)) (real, any leading axes)."""
+    Nz = x.shape[-1]
+    c = Nz // 2
+    w = int(np.ceil(pf * Nz)) - c
+    d = np.arange(Nz) - c
+    k = np.fft.fftshift(np.fft.fft(np.fft.ifftshift(x, axes=-1), axis=-1, norm="ortho"), axes=-1)
+    H = np.where(d < -w, 0.0, np.where(d <= w, 1.0, 2.0))
+    band = (np.abs(d) <= w).astype(float)
+
+    def ifftc(kk):
+        return np.fft.fftshift(np.fft.ifft(np.fft.ifftshift(kk, axes=-1), axis=-1, norm="ortho"), axes=-1)
+
+    h = ifftc(H * k)
+    lo = ifftc(band * k)
+    mag = np.abs(lo)
+    ph = np.where(mag > 0, np.conj(lo) / np.where(mag > 0, mag, 1.0), 1.0)
+    return (h * ph).real
+
+
+def postprocess(alpha: np.ndarray, maps: np.ndarray, phi: np.ndarray, te_index, pf: float) -> np.ndarray:
+    """TE images of one slice (Sec. III.C and the Reconstruction paragraph of Sec. V): coil
+    images at the listed echoes, homodyne along z per virtual coil, root sum of squares
+    over coils.  Returns [nte][Ny][Nz] (real)."""
+    xc = synthesize_te(alpha, maps, phi, te_index)
+    hd = homodyne_z(xc, pf)
+    return np.sqrt(np.sum(hd * hd, axis=1))
+
+
 def objective(alpha: np.ndarray, y: np.ndarray, maps: np.ndarray, mask: np.ndarray,
               phi: np.ndarray, lam: float, b: int, sy: int = 0, sz: int = 0) -> float:
     """Eq. 5 cost for T-form data y with the block grid of shift (sy, sz)."""

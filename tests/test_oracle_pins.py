@@ -472,3 +472,66 @@ def test_admm_and_fista_reach_the_same_convex_minimiser():
     assert np.abs(u - (aty - O.normal(v, maps, psi)) / rho).max() < 1e-7
     g = v - (O.normal(v, maps, psi) - aty) / rho
     assert np.abs(O.llr_prox(g, b, lam / rho, 0, 0) - v).max() < 1e-7
+
+
+# ----------------------------------------------------------------------------------
+# post-processing: TE synthesis, homodyne along z, root sum of squares
+# ----------------------------------------------------------------------------------
+def _real_positive_lines(rng, shape, nz, amp=0.3):
+    """Real lines 1 + amp * (random real band-limited signal without the Nyquist line):
+    positive enough that their low-pass stays positive."""
+    spec = crandn(rng, *shape, nz)
+    spec[..., nz // 2] = 0.0  # Nyquist line
+    x = np.fft.ifft(spec, axis=-1).real
+    x = x / np.abs(x).max()
+    return 1.0 + amp * x
+
+
+@pytest.mark.parametrize("nz,pf", [(48, 0.65), (40, 0.75), (64, 0.5625), (30, 0.7)])
+def test_homodyne_recovers_a_real_image_exactly(nz, pf):
+    """Real image without Nyquist content: the unpaired side weighted by 2 stands in for its
+    conjugate partners, so Re(IFFT(H k)) = x; its low-pass is positive, so the phase is 0."""
+    rng = np.random.default_rng(int(nz * 100 * pf))
+    x = _real_positive_lines(rng, (5,), nz)
+    # the Nyquist line of the centred transform is the index-0 line of the plain one
+    # after the half-length shift: check it is (numerically) empty
+    assert np.abs(np.fft.fft(np.fft.ifftshift(x, axes=-1), axis=-1)[..., nz // 2]).max() < 1e-9
+    out = O.homodyne_z(x.astype(complex), pf)
+    assert np.abs(out - x).max() < 1e-12
+    # a global phase is removed by the phase estimate
+    out2 = O.homodyne_z(x * np.exp(1j * 0.7), pf)
+    assert np.abs(out2 - x).max() < 1e-12
+
+
+def test_homodyne_full_fraction_is_the_magnitude():
+    rng = np.random.default_rng(9)
+    x = crandn(rng, 3, 8, 20)
+    assert np.abs(O.homodyne_z(x, 1.0) - np.abs(x)).max() < 1e-12
+
+
+def test_postprocess_full_fraction_is_rss_of_the_te_image():
+    """pf = 1 and sum_c |S_c|^2 = 1 per map set (M = 1): the RSS of the coil images is the
+    magnitude of the back-projected TE image."""
+    rng = np.random.default_rng(10)
+    T, K, C, ny, nz = 16, 4, 5, 12, 10
+    phi = synth.t2_basis(T, K)
+    maps = synth.coil_maps(C, ny, nz, rng)
+    alpha = crandn(rng, 1, K, ny, nz)
+    te = [2, 7, 15]
+    img = O.postprocess(alpha, maps, phi, te, 1.0)
+    xt = np.einsum("tk,kyz->tyz", phi[te], alpha[0])
+    assert np.abs(img - np.abs(xt)).max() < 1e-12
+
+
+def test_backprojection_reproduces_an_in_subspace_decay():
+    """x_t in the span of Phi (here Phi c): Phi Phi^T x_t = x_t, so the TE synthesis of
+    alpha = Phi^T x_t returns the decay itself (single coil, unit map)."""
+    rng = np.random.default_rng(11)
+    T, K, ny, nz = 20, 4, 6, 8
+    phi = synth.t2_basis(T, K)
+    cvec = crandn(rng, K, ny, nz)
+    xt = np.einsum("tk,kyz->tyz", phi, cvec)
+    alpha = np.einsum("tk,tyz->kyz", phi, xt)[None]
+    maps = np.ones((1, 1, ny, nz), complex)
+    got = O.synthesize_te(alpha, maps, phi, list(range(T)))[:, 0]
+    assert np.abs(got - xt).max() < 1e-12
