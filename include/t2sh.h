@@ -186,6 +186,26 @@ t2sh_status t2sh_solve_admm(t2sh_plan_t plan, const void* kspace, int32_t kform,
                             int32_t cg_iters, double* residual_out);
 
 /*
+ * t2sh_postprocess -- TE images from reconstructed coefficients (the "Process TE" step of
+ * Sec. III.C and the Reconstruction paragraph of Sec. V): for each requested echo
+ * te_index[i] (rows of the plan's basis Phi, 0-based) and each slice,
+ *   x_m(t) = sum_k Phi[t][k] alpha[m][k]          back-projection with the basis (Eq. 3)
+ *   x_c(t) = sum_m S_{c,m} x_m(t)                  virtual-coil images
+ *   homodyne detection along z (the slice direction, partial Fourier fraction pf in
+ *   (1/2, 1]): centred unitary DFT along z, acquired lines d in [-w, nz/2) with
+ *   w = ceil(pf nz) - nz/2 (computed in double from the float pf), weighting 0 / 1 / 2
+ *   outside / inside / beyond the two-sided band |d| <= w, phase from the band alone,
+ *   result Re(IFFT(H k) exp(-i phase))
+ *   out = sqrt(sum_c homodyne(x_c(t))^2)           root sum of squares
+ * alpha: device [S][M][K][ny][nz] complex64; out: device [S][nte][ny][nz] float32 (caller
+ * owned).  1 <= nte <= 8.  Asynchronous on the plan's stream.  Plans made with
+ * T2SH_HOST_IO return T2SH_EUNSUPPORTED.  (The paper's 3D wavelet denoising before this
+ * step works across readout slices and is not part of it.)
+ */
+t2sh_status t2sh_postprocess(t2sh_plan_t plan, const void* alpha, const int32_t* te_index, int32_t nte, float pf,
+                             void* out);
+
+/*
  * Resumable solve, for schedulers that interleave several scans (t2sh_solve is
  * t2sh_solve_begin + t2sh_solve_iterate(dims.iters) + t2sh_solve_end):
  *   t2sh_solve_begin    forms A^H y from the k-space (as t2sh_solve) and resets the FISTA
@@ -269,6 +289,7 @@ t2sh_status t2sh_workspace_bytes(const t2sh_dims* dims, size_t* bytes);
  *   5 projection of per-echo k-space
  *   6 fused band kernel of t2sh_solve (row adjoint + gradient + LLR + momentum + row forward)
  *   7 conjugate-gradient vector kernels of t2sh_solve_admm
+ *   8 TE-image post-processing (t2sh_postprocess)
  * t2sh_timing_enable(plan, 1) clears the counters and starts recording; (plan, 0) stops.
  * t2sh_timing_read synchronises the stream and returns the launch count and the summed
  * event-to-event milliseconds of one class since the last enable.  Recording adds two

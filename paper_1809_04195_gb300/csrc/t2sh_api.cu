@@ -178,12 +178,12 @@ struct t2sh_plan_s {
   bool record_res = false;
   bool fused_rows = false;  // tunable: fused band kernel for the row work
   // kernel timing (t2sh_timing_*)
-  static constexpr int kClasses = 8;
+  static constexpr int kClasses = 9;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   size_t ev_next = 0;
-  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t launches[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   // ADMM state (allocated on the first t2sh_solve_admm): scaled dual u, CG residual and
   // direction, per-slice float64 accumulators rr[3][S] and pq[S]
   float2* u = nullptr;
@@ -241,7 +241,7 @@ struct KTimer {
     }
   }
 };
-enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5, KC_BAND = 6, KC_CG = 7 };
+enum { KC_ROW_FWD = 0, KC_ROW_ADJ = 1, KC_COL = 2, KC_LLR = 3, KC_PLAN = 4, KC_PROJ = 5, KC_BAND = 6, KC_CG = 7, KC_POST = 8 };
 }  // namespace
 
 namespace {
@@ -676,6 +676,32 @@ t2sh_status t2sh_solve_admm(t2sh_plan_t p, const void* kspace, int32_t kform, vo
   s = end_impl(p, alpha_out, residual_out, p->z);
   p->begun = false;  // the FISTA state was not kept: no t2sh_solve_iterate on top of this
   return s;
+}
+
+t2sh_status t2sh_postprocess(t2sh_plan_t p, const void* alpha, const int32_t* te_index, int32_t nte, float pf,
+                             void* out) {
+  T2SH_REQ(p && alpha && te_index && out, "NULL argument");
+  const t2sh_dims& d = p->d;
+  if (p->host_io) {
+    set_err("t2sh_postprocess takes device pointers (the plan has T2SH_HOST_IO)");
+    return T2SH_EUNSUPPORTED;
+  }
+  T2SH_REQ(nte >= 1 && nte <= kMaxPostTe, "nte must be in [1, %d]", kMaxPostTe);
+  for (int i = 0; i < nte; ++i)
+    T2SH_REQ(te_index[i] >= 0 && te_index[i] < d.nechoes, "te_index[%d] = %d is not an echo of the basis", i, te_index[i]);
+  T2SH_REQ(std::isfinite(pf) && pf > 0.5f && pf <= 1.f, "pf must be in (0.5, 1]");
+  if (post_smem_bytes(p->g, nte) > 200 * 1024) {
+    set_err("post-processing band of %d echoes x nz = %d does not fit shared memory", nte, d.nz);
+    return T2SH_EUNSUPPORTED;
+  }
+  // band half-width, decided in double from the float fraction
+  const int w = (int)std::ceil((double)pf * (double)d.nz) - d.nz / 2;
+  int te[kMaxPostTe];
+  for (int i = 0; i < nte; ++i) te[i] = te_index[i];
+  KTimer k(p, KC_POST);
+  T2SH_CK(launch_post(p->g, p->pz, p->tw_z, p->maps, p->phi, static_cast<const float2*>(alpha), te, nte, w,
+                      static_cast<float*>(out), p->st));
+  return T2SH_OK;
 }
 
 t2sh_status t2sh_solve_begin(t2sh_plan_t p, const void* kspace, int32_t kform) {

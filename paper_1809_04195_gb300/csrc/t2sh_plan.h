@@ -16,6 +16,7 @@ constexpr int kMaxPass = 8;
 constexpr int kMaxK = 8;
 constexpr int kMaxM = 2;
 constexpr int kMaxBlock = 16;
+constexpr int kMaxPostTe = 8;                    // echoes one t2sh_postprocess call synthesises
 
 // Radix plan of a length-n FFT: pass q has radix radix[q] and ns[q] = prod of the
 // radices of passes 0..q-1 (Stockham autosort).
@@ -78,6 +79,11 @@ cudaError_t launch_row(const Geom& g, RowMode mode, const FftPlan& pz, const flo
                        const float2* x, float2* t, float2* out, cudaStream_t st);
 cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const float2* tw_y, const float* psi,
                        const float* phi, const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st);
+// TE images: back-projection at echoes te[0..nte), coil images, homodyne along z with
+// band half-width w, root sum of squares -> out [S][nte][ny][nz] float
+size_t post_smem_bytes(const Geom& g, int nte);
+cudaError_t launch_post(const Geom& g, const FftPlan& pz, const float2* tw_z, const float2* maps, const float* phi,
+                        const float2* alpha, const int* te, int nte, int w, float* out, cudaStream_t st);
 // ADMM v-update: w = alpha + u, v = LLR prox of w (threshold a.tau, shift a.sy/a.sz), u <- w - v
 cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alpha, float2* v, float2* u,
                             cudaStream_t st);

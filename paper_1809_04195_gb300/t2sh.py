@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
             "t2sh_llr_prox": [_vp, _vp, _f32, _i32, _i32],
             "t2sh_solve": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
             "t2sh_solve_admm": [_vp, _vp, _i32, _vp, _f32, _i32, ctypes.POINTER(ctypes.c_double)],
+            "t2sh_postprocess": [_vp, _vp, ctypes.POINTER(_i32), _i32, _f32, _vp],
             "t2sh_get_step": [_vp, ctypes.POINTER(_f32)],
             "t2sh_shifts": [_u64, _i32, _i32, ctypes.POINTER(_i32)],
             "t2sh_workspace_bytes": [ctypes.POINTER(Dims), ctypes.POINTER(ctypes.c_size_t)],
@@ -285,6 +286,20 @@ class Plan:
         _check(lib().t2sh_solve_admm(self._h, kp, kform, op, float(rho), int(cg_iters), rp))
         return (out, res) if residual else out
 
+    def postprocess(self, alpha, te_index, pf: float = 0.65, out=None):
+        """TE images [S][nte][ny][nz] (float32, device): back-projection at the echoes
+        te_index, coil images, homodyne along z (partial Fourier fraction pf), RSS."""
+        import torch
+        te = list(int(t) for t in te_index)
+        shape = (self.S, len(te), self.ny, self.nz)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        ap = self._dev(alpha, self.vec_shape)
+        op = _ptr(out, torch.float32, shape, False)
+        tarr = (_i32 * len(te))(*te)
+        _check(lib().t2sh_postprocess(self._h, ap, tarr, len(te), float(pf), op))
+        return out
+
     # -- resumable solve (schedulers interleaving scans) --------------------------------
     def solve_begin(self, kspace, kform=KSPACE_PROJ):
         import torch
@@ -329,7 +344,7 @@ class Plan:
         _check(lib().t2sh_sync(self._h))
 
     # -- kernel timing ----------------------------------------------------------------
-    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band", 7: "cg"}
+    KERNEL_CLASSES = {0: "row_fwd", 1: "row_adj", 2: "col", 3: "llr", 5: "project", 6: "band", 7: "cg", 8: "post"}
 
     def timing(self, enable: bool):
         _check(lib().t2sh_timing_enable(self._h, 1 if enable else 0))
