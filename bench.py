@@ -50,6 +50,8 @@ def parse():
                     help="admm: t2sh_solve_admm (CG alpha-updates); an iteration is one outer ADMM iteration")
     ap.add_argument("--rho", type=float, default=0.5)
     ap.add_argument("--cg-iters", type=int, default=3)
+    ap.add_argument("--post-te", default="",
+                    help="comma-separated echo indices: each step also forms TE images (t2sh_postprocess, pf 0.65)")
     ap.add_argument("--workload", choices=["knee", "paper"], default="knee",
                     help="paper: the Table I scan (288 slices of 260x240, C=7, M=2, b=12, 250 iterations)")
     return ap.parse_args()
@@ -254,6 +256,9 @@ def run_ours(args):
     dims1 = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=1, nmaps=sh.nmaps, block=sh.block,
                            lam=sh.lam, iters=iters, seed=sh.seed, precision=prec)
 
+    post_te = [int(t) for t in args.post_te.split(",") if t.strip()]
+    img_d = (torch.empty((S, len(post_te), sh.ny, sh.nz), dtype=torch.float32, device=dev) if post_te else None)
+
     def step(timing):
         if args.form == "per-slice":  # every slice its own plan and solve, one after the other
             tm = {}
@@ -276,6 +281,8 @@ def run_ours(args):
             p.solve_admm(ytil_d, t2sh.KSPACE_PROJ, rho=args.rho, cg_iters=args.cg_iters, out=out_d)
         else:
             p.solve(ytil_d, t2sh.KSPACE_PROJ, out=out_d)
+        if post_te:
+            p.postprocess(out_d, post_te, pf=0.65, out=img_d)
         tm = p.timing_read() if timing else None
         p.close()
         return tm
@@ -369,7 +376,8 @@ def run_ours(args):
             "dtype": "f32" if prec == t2sh.FP32 else "f32 + bf16x3 (column DFTs on tensor cores, f32 accumulate)",
             "data": "synthetic (seeded 3D ellipsoid knee phantom, smooth coil maps, variable-density masks)",
             "config": {**config_dict(sh, S, iters, world), "precision": args.precision, "form": args.form,
-                       **({"solver": f"admm rho={args.rho} cg_iters={args.cg_iters}"} if args.solver == "admm" else {})}, "roofline": roof, "gpu_launches": launches,
+                       **({"solver": f"admm rho={args.rho} cg_iters={args.cg_iters}"} if args.solver == "admm" else {}),
+                       **({"post_te": post_te} if post_te else {})}, "roofline": roof, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": e2e}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sh)

@@ -43,13 +43,13 @@ def test_postprocess_matches_oracle(T, S, ny, nz, C, Tn, K, M, pf, te):
 
 
 def test_postprocess_of_a_reconstruction(T):
-    """TE images (PD / intermediate / T2-weighted: echoes 3, 8, 15 of a 6 ms echo train,
-    the paper's 21, 50 and 90 ms) of the solved knee slices."""
+    """TE images (PD / intermediate / T2-weighted: echoes 3, 9, 17 of the 5 ms synthetic
+    echo train, 20 / 50 / 90 ms for the paper's 21 / 50 / 90 ms) of the solved knee slices."""
     sh = synth.KNEE_320x256x160
     sl = [0, 160]
     phi, mask, maps, ytil = proj_scan(sh, sl)
     phi, maps = r32(phi, maps)
-    te = [3, 8, 15]
+    te = [3, 9, 17]
     with make_plan(T, phi, mask, maps, block=sh.block, lam=sh.lam, iters=20, seed=sh.seed) as p:
         alpha = p.solve(c64(ytil), T.KSPACE_PROJ)
         img = p.postprocess(alpha, te, pf=0.65).cpu().numpy().astype(np.float64)
