@@ -352,11 +352,15 @@ def run_ours(args):
 
     peaks, src = measured_peaks()
     ab = algorithmic_bytes(1 if args.form == "per-slice" else S, sh.ncoils, sh.nmaps, sh.nbasis, N)
+    if post_te:  # per echo: alpha and the maps read once, the float image written
+        Sx = 1 if args.form == "per-slice" else S
+        ab["post"] = len(post_te) * (Sx * sh.nmaps * (sh.nbasis + sh.ncoils) * N * 8 + Sx * N * 4)
     if args.solver == "admm":
         vec = (1 if args.form == "per-slice" else S) * sh.nmaps * sh.nbasis * N * 8
         ab["llr"] = 4 * vec  # read alpha, u; write v, u
-        # per outer iteration: init (5 reads, 2 writes) + cg_iters x (dot 2, step 4 + 2, dir 2 + 1)
-        ab["cg"] = (7 + 11 * args.cg_iters) * vec / (1 + 3 * args.cg_iters)
+        # per outer iteration: init (5 reads, 2 writes) + cg_iters x (dot 2, step 4 + 2, dir 2 + 1);
+        # the "cg" timing class counts the init and each CG iteration's three kernels as one unit
+        ab["cg"] = (7 + 11 * args.cg_iters) * vec / (1 + args.cg_iters)
     kern = {k: {"launches": n, "ms_total": m, "ms_per_launch": (m / n if n else None),
                 "algorithmic_bytes_per_launch": ab.get(k)} for k, (n, m) in totals.items() if n}
     dom = max((k for k in kern if k in ab), key=lambda k: kern[k]["ms_total"])

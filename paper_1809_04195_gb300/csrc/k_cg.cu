@@ -15,7 +15,7 @@ namespace t2sh {
 namespace {
 
 constexpr int kCgThreads = 256;
-constexpr int kCgPerThread = 4;  // float4 loads per thread per vector
+constexpr int kCgPerThread = 2;  // float4 loads per thread per vector
 
 __device__ __forceinline__ void block_add(double v, double* out) {
   __shared__ double part[kCgThreads / 32];
@@ -37,7 +37,17 @@ __device__ __forceinline__ void st4(float2* p, long long i, float4 v) { *reinter
 __device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 
 // Every kernel first issues all of its loads (kCgPerThread float4 per vector), then
-// computes and stores, so that each thread keeps its loads in flight together.
+// computes and stores, so that each thread keeps its loads in flight together.  The
+// per-slice quotient (a float64 division) is formed once per CTA and broadcast.
+__device__ __forceinline__ float cta_quotient(const double* num, const double* den, int s) {
+  __shared__ float q;
+  if (threadIdx.x == 0) {
+    const double d = den[s];
+    q = d != 0.0 ? (float)(num[s] / d) : 0.f;
+  }
+  __syncthreads();
+  return q;
+}
 #define CG_INDEX(i) (2 * ((long long)(blockIdx.x * kCgPerThread + (i)) * kCgThreads + threadIdx.x))
 
 // r = aty + rho (v - u) - w - rho x  (w = A^H A x);  p = r;  rr[s] += |r|^2
@@ -112,8 +122,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_step(long long L, float2* __r
       xa[i] = ld4(x, base + e); ra[i] = ld4(r, base + e);
     }
   }
-  const double den = pq[s];
-  const float a = den != 0.0 ? (float)(rr[s] / den) : 0.f;
+  const float a = cta_quotient(rr, pq, s);
   float acc = 0.f;
 #pragma unroll
   for (int i = 0; i < kCgPerThread; ++i) {
@@ -151,8 +160,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_dir(long long L, const float2
       pa[i] = ld4(p, base + e);
     }
   }
-  const double den = rr[s];
-  const float b = den != 0.0 ? (float)(rr_new[s] / den) : 0.f;
+  const float b = cta_quotient(rr_new, rr, s);
 #pragma unroll
   for (int i = 0; i < kCgPerThread; ++i) {
     const long long e = CG_INDEX(i);

@@ -21,7 +21,7 @@ struct RowCaps {
   static constexpr int PMAX = (KC * MC <= 4) ? 4 : (KC * MC <= 8 ? 2 : 1);
 };
 
-template <int MODE, int KC, int MC>
+template <int MODE, int KC, int MC, bool R13>
 __global__ void __launch_bounds__(kFftThreads) k_row(Geom g, FftPlan pz, const float2* __restrict__ tw_g,
                                                    const float2* __restrict__ maps, const float2* __restrict__ x,
                                                    float2* __restrict__ t, float2* __restrict__ out, int RB) {
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kFftThreads) k_row(Geom g, FftPlan pz, const f
         }
       }
       __syncthreads();
-      fft_lines<false>(lbuf, ld, K * rb, pz, tw);
+      fft_lines<false, R13>(lbuf, ld, K * rb, pz, tw);
       for (int e = threadIdx.x; e < nelem2; e += kFftThreads) {
         const int e0 = 2 * e;
         const int k = e0 / npix;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kFftThreads) k_row(Geom g, FftPlan pz, const f
       }
       __syncthreads();
     } else {
-      fft_lines<true>(lbuf, ld, K * rb, pz, tw);
+      fft_lines<true, R13>(lbuf, ld, K * rb, pz, tw);
 #pragma unroll
       for (int u = 0; u < PMAX; ++u) {
         if (pr[u] >= 0) {
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kFftThreads) k_row(Geom g, FftPlan pz, const f
 // Normal-operator column pass, persistent and double buffered: each CTA walks the
 // (slice, coil, column tile) list; the next tile streams into shared memory with
 // cp.async while the current one is transformed (DFT_y, Psi, IDFT_y) and written back.
-template <int KC>
+template <int KC, bool R13>
 __global__ void __launch_bounds__(kFftThreads, 1) k_col_normal(Geom g, FftPlan py, const float2* __restrict__ tw_g,
                                                              const float* __restrict__ psi, float2* t, int W,
                                                              int ntz, int ntiles) {
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_col_normal(Geom g, FftPlan p
     __syncthreads();
     const int sc = tile / ntz, zt = tile - sc * ntz;
     const int z0 = zt * W, wc = min(W, nz - z0);
-    fft_lines<false>(buf, ld, K * wc, py, tw);
+    fft_lines<false, R13>(buf, ld, K * wc, py, tw);
     const int npt = ny * wc;
     for (int q = threadIdx.x; q < npt; q += kFftThreads) {
       const int w = q % wc, y = q / wc;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_col_normal(Geom g, FftPlan p
         if (k < K) buf[(k * wc + w) * ld + y] = u[k];
     }
     __syncthreads();
-    fft_lines<true>(buf, ld, K * wc, py, tw);
+    fft_lines<true, R13>(buf, ld, K * wc, py, tw);
     float2* ob = t + (long long)sc * K * N + z0;
     const int nel = K * ny * wc;
     for (int e = threadIdx.x; e < nel; e += kFftThreads) {
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_col_normal(Geom g, FftPlan p
 
 // Column pass.  tin/tout are [S][C][K][ny][nz] (may alias); FWD_TE writes yout
 // [S][C][T][ny][nz] and FWD_PROJ writes yout [S][C][K][ny][nz].
-template <int MODE, int KC>
+template <int MODE, int KC, bool R13>
 __global__ void __launch_bounds__(kFftThreads) k_col(Geom g, FftPlan py, const float2* __restrict__ tw_g,
                                                 const float* __restrict__ psi, const float* __restrict__ phi,
                                                 const uint8_t* __restrict__ mask, const float2* tin, float2* tout,
@@ -271,9 +271,9 @@ __global__ void __launch_bounds__(kFftThreads) k_col(Geom g, FftPlan py, const f
   }
   __syncthreads();
   if (MODE == COL_ADJ_DATA) {
-    fft_lines<true>(buf, ld, K * wc, py, tw);
+    fft_lines<true, R13>(buf, ld, K * wc, py, tw);
   } else {
-    fft_lines<false>(buf, ld, K * wc, py, tw);
+    fft_lines<false, R13>(buf, ld, K * wc, py, tw);
     const int npt = ny * wc;
     if (MODE == COL_NORMAL || MODE == COL_FWD_PROJ) {
       const float pscale = (MODE == COL_FWD_PROJ) ? (float)N : 1.0f;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kFftThreads) k_col(Geom g, FftPlan py, const f
       }
       __syncthreads();
       if (MODE == COL_FWD_PROJ) return;
-      fft_lines<true>(buf, ld, K * wc, py, tw);
+      fft_lines<true, R13>(buf, ld, K * wc, py, tw);
     } else {  // COL_FWD_TE
       for (int q = threadIdx.x; q < npt; q += kFftThreads) {
         const int w = q % wc, y = q / wc;
@@ -366,21 +366,28 @@ int col_cols_per_cta(const Geom& g) {
   return w;
 }
 
-template <int MODE, int KC, int MC>
-static cudaError_t row_go(const Geom& g, const FftPlan& pz, const float2* tw, const float2* maps, const float2* x,
-                          float2* t, float2* out, cudaStream_t st) {
+template <int MODE, int KC, int MC, bool R13>
+static cudaError_t row_go13(const Geom& g, const FftPlan& pz, const float2* tw, const float2* maps, const float2* x,
+                            float2* t, float2* out, cudaStream_t st) {
   const int RB = row_rows_per_cta(g);
   const size_t lines = (((size_t)g.K * RB * (g.nz + 1) + 1) & ~(size_t)1) * (MODE == ROW_ADJ ? 2 : 1);
   const size_t sm = sizeof(float2) * (((g.nz + 1) & ~1) + lines + 2 * (size_t)g.M * RB * g.nz);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_row<MODE, KC, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_row<MODE, KC, MC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((g.ny + RB - 1) / RB, g.S);
-  k_row<MODE, KC, MC><<<grid, kFftThreads, sm, st>>>(g, pz, tw, maps, x, t, out, RB);
+  k_row<MODE, KC, MC, R13><<<grid, kFftThreads, sm, st>>>(g, pz, tw, maps, x, t, out, RB);
   return cudaGetLastError();
+}
+
+template <int MODE, int KC, int MC>
+static cudaError_t row_go(const Geom& g, const FftPlan& pz, const float2* tw, const float2* maps, const float2* x,
+                          float2* t, float2* out, cudaStream_t st) {
+  return plan_has13(pz) ? row_go13<MODE, KC, MC, true>(g, pz, tw, maps, x, t, out, st)
+                        : row_go13<MODE, KC, MC, false>(g, pz, tw, maps, x, t, out, st);
 }
 
 cudaError_t launch_row(const Geom& g, RowMode mode, const FftPlan& pz, const float2* tw_z, const float2* maps,
@@ -400,31 +407,38 @@ cudaError_t launch_row(const Geom& g, RowMode mode, const FftPlan& pz, const flo
   return row_go<ROW_ADJ, 8, 2>(g, pz, tw_z, maps, x, t, out, st);
 }
 
-template <int MODE, int KC>
-static cudaError_t col_go(const Geom& g, const FftPlan& py, const float2* tw, const float* psi, const float* phi,
-                          const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st) {
+template <int MODE, int KC, bool R13>
+static cudaError_t col_go13(const Geom& g, const FftPlan& py, const float2* tw, const float* psi, const float* phi,
+                            const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st) {
   const int W = col_cols_per_cta(g);
   const size_t sm = sizeof(float2) * (((g.ny + 1) & ~1) + (size_t)g.K * W * (g.ny + 1));
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_col<MODE, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_col<MODE, KC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((g.nz + W - 1) / W, g.C, g.S);
-  k_col<MODE, KC><<<grid, kFftThreads, sm, st>>>(g, py, tw, psi, phi, mask, tin, tout, W);
+  k_col<MODE, KC, R13><<<grid, kFftThreads, sm, st>>>(g, py, tw, psi, phi, mask, tin, tout, W);
   return cudaGetLastError();
 }
 
-template <int KC>
-static cudaError_t col_normal_go(const Geom& g, const FftPlan& py, const float2* tw, const float* psi, float2* t,
-                                 cudaStream_t st) {
+template <int MODE, int KC>
+static cudaError_t col_go(const Geom& g, const FftPlan& py, const float2* tw, const float* psi, const float* phi,
+                          const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st) {
+  return plan_has13(py) ? col_go13<MODE, KC, true>(g, py, tw, psi, phi, mask, tin, tout, st)
+                        : col_go13<MODE, KC, false>(g, py, tw, psi, phi, mask, tin, tout, st);
+}
+
+template <int KC, bool R13>
+static cudaError_t col_normal_go13(const Geom& g, const FftPlan& py, const float2* tw, const float* psi, float2* t,
+                                   cudaStream_t st) {
   const int W = col_cols_per_cta(g);
   const size_t sm = sizeof(float2) * (((g.ny + 1) & ~1) + 2 * (size_t)g.K * W * (g.ny + 1));
   static int grid_per_sm = 0;
   static int nsm = 0;
   if (!grid_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_normal<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_col_normal<KC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     int dev = 0;
     e = cudaGetDevice(&dev);
@@ -432,7 +446,7 @@ static cudaError_t col_normal_go(const Geom& g, const FftPlan& py, const float2*
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_normal<KC>, kFftThreads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_normal<KC, R13>, kFftThreads, sm);
     if (e != cudaSuccess) return e;
     grid_per_sm = per > 0 ? per : 1;
   }
@@ -440,8 +454,15 @@ static cudaError_t col_normal_go(const Geom& g, const FftPlan& py, const float2*
   const long long ntiles = (long long)g.S * g.C * ntz;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)nsm * grid_per_sm);
-  k_col_normal<KC><<<grid, kFftThreads, sm, st>>>(g, py, tw, psi, t, W, ntz, (int)ntiles);
+  k_col_normal<KC, R13><<<grid, kFftThreads, sm, st>>>(g, py, tw, psi, t, W, ntz, (int)ntiles);
   return cudaGetLastError();
+}
+
+template <int KC>
+static cudaError_t col_normal_go(const Geom& g, const FftPlan& py, const float2* tw, const float* psi, float2* t,
+                                 cudaStream_t st) {
+  return plan_has13(py) ? col_normal_go13<KC, true>(g, py, tw, psi, t, st)
+                        : col_normal_go13<KC, false>(g, py, tw, psi, t, st);
 }
 
 cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const float2* tw_y, const float* psi,

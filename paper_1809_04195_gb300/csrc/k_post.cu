@@ -26,7 +26,7 @@ struct PostArgs {
   int w;  // half-width of the two-sided band
 };
 
-template <int MC>
+template <int MC, bool R13>
 __global__ void __launch_bounds__(kPostThreads) k_post(Geom g, FftPlan pz, const float2* __restrict__ tw_g,
                                                      const float2* __restrict__ maps, const float* __restrict__ phi,
                                                      const float2* __restrict__ alpha, PostArgs pa,
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(Geom g, FftPlan pz, const
         lines[r * ld + z] = v;
       }
       __syncthreads();
-      fft_lines<false>(lines, ld, rb, pz, tw);
+      fft_lines<false, R13>(lines, ld, rb, pz, tw);
       for (int q = threadIdx.x; q < npt; q += kPostThreads) {
         const int r = q / nz, k = q - r * nz, d = k - c0;
         const float2 v = lines[r * ld + k];
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(Geom g, FftPlan pz, const
         lines[r * ld + k] = make_float2(hw * v.x, hw * v.y);
       }
       __syncthreads();
-      fft_lines<true>(lines, ld, kPostRB + rb, pz, tw);  // h lines 0..rb-1, band lines RB..RB+rb-1
+      fft_lines<true, R13>(lines, ld, kPostRB + rb, pz, tw);  // h lines 0..rb-1, band lines RB..RB+rb-1
       const float inv_n = 1.f / (float)nz;
       for (int q = threadIdx.x; q < npt; q += kPostThreads) {
         const int r = q / nz, z = q - r * nz;
@@ -97,6 +97,19 @@ __global__ void __launch_bounds__(kPostThreads) k_post(Geom g, FftPlan pz, const
     const int ti = e / npt, q = e - ti * npt, r = q / nz, z = q - r * nz;
     out[((long long)s * pa.nte + ti) * N + (long long)(y0 + r) * nz + z] = sqrtf(acc[(ti * kPostRB + r) * nz + z]);
   }
+}
+
+template <int MC, bool R13>
+cudaError_t post_go(const Geom& g, const FftPlan& pz, const float2* tw_z, const float2* maps, const float* phi,
+                    const float2* alpha, const PostArgs& pa, float* out, dim3 grid, size_t sm, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_post<MC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_post<MC, R13><<<grid, kPostThreads, sm, st>>>(g, pz, tw_z, maps, phi, alpha, pa, out);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -116,24 +129,13 @@ cudaError_t launch_post(const Geom& g, const FftPlan& pz, const float2* tw_z, co
   pa.w = w;
   const size_t sm = post_smem_bytes(g, nte);
   dim3 grid((g.ny + kPostRB - 1) / kPostRB, g.S);
+  const bool r13 = plan_has13(pz);
   if (g.M == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_post<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_post<1><<<grid, kPostThreads, sm, st>>>(g, pz, tw_z, maps, phi, alpha, pa, out);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_post<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_post<2><<<grid, kPostThreads, sm, st>>>(g, pz, tw_z, maps, phi, alpha, pa, out);
+    if (r13) return post_go<1, true>(g, pz, tw_z, maps, phi, alpha, pa, out, grid, sm, st);
+    return post_go<1, false>(g, pz, tw_z, maps, phi, alpha, pa, out, grid, sm, st);
   }
-  return cudaGetLastError();
+  if (r13) return post_go<2, true>(g, pz, tw_z, maps, phi, alpha, pa, out, grid, sm, st);
+  return post_go<2, false>(g, pz, tw_z, maps, phi, alpha, pa, out, grid, sm, st);
 }
 
 }  // namespace t2sh

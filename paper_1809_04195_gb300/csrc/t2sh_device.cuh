@@ -245,14 +245,15 @@ __device__ __forceinline__ void dft_r(float2* v) {
 // the twiddle read is a broadcast.  Requires nbatch * p.n <= kStage * blockDim.x.
 //   tw[m] = exp(-2 pi i m / n), m < n (shared memory copy).
 // ---------------------------------------------------------------------------------
-constexpr int kStageRegs = 26;  // >= ceil(kStage / R) * R for every radix used (13: 2 x 13)
+constexpr int kStageRegs = 20;    // >= ceil(kStage / R) * R for the radices 2, 3, 4, 5, 8, 16
+constexpr int kStageRegs13 = 26;  // with radix 13 (2 x 13): only plans that contain a radix-13 pass
 constexpr int kStageBf = 8;     // >= ceil(kStage / R) for every radix used
 
-template <int R, bool INV>
+template <int R, bool INV, int NV>
 __device__ __forceinline__ void stockham_pass(float2* buf, int ld, int nbatch, int n, int ns, const float2* tw,
-                                              float2 (&v)[kStageRegs], int (&dst)[kStageBf]) {
+                                              float2 (&v)[NV], int (&dst)[kStageBf]) {
   constexpr int UMAX = (kStage + R - 1) / R;
-  static_assert(UMAX * R <= kStageRegs && UMAX <= kStageBf, "staging registers");
+  static_assert(UMAX * R <= NV && UMAX <= kStageBf, "staging registers");
   const int nbf = n / R;
   const int total = nbf * nbatch;
   const int tstride = n / (ns * R);
@@ -287,20 +288,25 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int ld, int nbatch, i
   __syncthreads();
 }
 
-template <bool INV>
+// R13: the plan may contain a radix-13 pass (wider staging; a separate instantiation so
+// that plans without one keep the smaller register footprint)
+template <bool INV, bool R13 = false>
 __device__ __forceinline__ void fft_lines(float2* buf, int ld, int nbatch, const FftPlan& p, const float2* tw) {
-  float2 v[kStageRegs];
+  constexpr int NV = R13 ? kStageRegs13 : kStageRegs;
+  float2 v[NV];
   int dst[kStageBf];
   for (int q = 0; q < p.npass; ++q) {
     const int ns = p.ns[q];
     switch (p.radix[q]) {
-      case 16: stockham_pass<16, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
-      case 8: stockham_pass<8, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
-      case 4: stockham_pass<4, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
-      case 2: stockham_pass<2, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
-      case 3: stockham_pass<3, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
-      case 5: stockham_pass<5, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
-      case 13: stockham_pass<13, INV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 16: stockham_pass<16, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 8: stockham_pass<8, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 4: stockham_pass<4, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 2: stockham_pass<2, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 3: stockham_pass<3, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 5: stockham_pass<5, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst); break;
+      case 13:
+        if constexpr (R13) stockham_pass<13, INV, NV>(buf, ld, nbatch, p.n, ns, tw, v, dst);
+        break;
       default: break;
     }
   }

@@ -27,6 +27,12 @@ struct FftPlan {
   int ns[kMaxPass];
 };
 
+inline bool plan_has13(const FftPlan& p) {
+  for (int q = 0; q < p.npass; ++q)
+    if (p.radix[q] == 13) return true;
+  return false;
+}
+
 // Geometry of one batch of slices, passed by value to every kernel.
 struct Geom {
   int S, C, M, K, T;   // slices, coils, map sets, basis size, echoes
