@@ -362,6 +362,62 @@ def postprocess(alpha: np.ndarray, maps: np.ndarray, phi: np.ndarray, te_index, 
     return np.sqrt(np.sum(hd * hd, axis=1))
 
 
+# ----------------------------------------------------------------------------------
+# Pre-processing (Sec. III.A): the acquisition is a sparse array of fully sampled
+# readout lines, line j holding the channels [Ctot][Nx] of phase encode (ky_j, kz_j) at
+# echo t_j.  Index conventions: DC of every axis at index N/2.
+# ----------------------------------------------------------------------------------
+def calibration_average(lines: np.ndarray, ky, kz, ny: int, nz: int, win: int) -> np.ndarray:
+    """Re-sort and average: the central win x win x win k-space window of every channel,
+    each (ky, kz) averaged over the lines (echoes) that sampled it, unsampled points zero.
+    lines [n][Ctot][Nx]; returns [Ctot][win][win][win] (axes kx, ky, kz)."""
+    n, ctot, nx = lines.shape
+    cal = np.zeros((ctot, win, win, win), np.complex128)
+    cnt = np.zeros((win, win))
+    x0, y0, z0 = nx // 2 - win // 2, ny // 2 - win // 2, nz // 2 - win // 2
+    for j in range(n):
+        a, b = int(ky[j]) - y0, int(kz[j]) - z0
+        if 0 <= a < win and 0 <= b < win:
+            cal[:, :, a, b] += lines[j, :, x0:x0 + win]
+            cnt[a, b] += 1
+    return cal / np.where(cnt > 0, cnt, 1.0)[None, None]
+
+
+def compression_matrix(cal: np.ndarray, ncomp: int) -> np.ndarray:
+    """SVD coil compression (Zhang et al. 2013): with the calibration points as rows of
+    X [points][Ctot], the virtual channels are X W[:, :ncomp], W the right singular
+    vectors (eigenvectors of X^H X) by decreasing singular value.  Each column is fixed
+    to a canonical phase: its entry of largest magnitude (first such index) is real
+    positive.  Returns W [Ctot][ncomp]."""
+    ctot = cal.shape[0]
+    X = cal.reshape(ctot, -1).T
+    G = X.conj().T @ X
+    ev, V = np.linalg.eigh(G)
+    V = V[:, np.argsort(-ev)[:ncomp]]
+    for c in range(ncomp):
+        i = int(np.argmax(np.abs(V[:, c])))
+        V[:, c] *= np.conj(V[i, c]) / np.abs(V[i, c])
+    return V
+
+
+def preprocess(lines: np.ndarray, t_idx, ky, kz, W: np.ndarray, phi: np.ndarray, ny: int, nz: int):
+    """Coil-compress every line (y_v = y W), decouple the readout slices by the centred
+    unitary 1D inverse DFT along x, and re-sort and project onto the basis:
+    ytil[x][c][k][ky][kz] = sum over lines j at (ky, kz) of Phi[t_j][k] yhat_j[c][x].
+    Also the sampling masks mask[t][ky][kz].  Returns (ytil [Nx][C][K][Ny][Nz], mask)."""
+    n, ctot, nx = lines.shape
+    T, K = phi.shape
+    C = W.shape[1]
+    yv = np.einsum("jcx,cd->jdx", lines, W)
+    yh = np.fft.fftshift(np.fft.ifft(np.fft.ifftshift(yv, axes=-1), axis=-1, norm="ortho"), axes=-1)
+    ytil = np.zeros((nx, C, K, ny, nz), np.complex128)
+    mask = np.zeros((T, ny, nz), np.uint8)
+    for j in range(n):
+        ytil[:, :, :, ky[j], kz[j]] += np.einsum("k,cx->xck", phi[t_idx[j]], yh[j])
+        mask[t_idx[j], ky[j], kz[j]] = 1
+    return ytil, mask
+
+
 def objective(alpha: np.ndarray, y: np.ndarray, maps: np.ndarray, mask: np.ndarray,
               phi: np.ndarray, lam: float, b: int, sy: int = 0, sz: int = 0) -> float:
     """Eq. 5 cost for T-form data y with the block grid of shift (sy, sz)."""

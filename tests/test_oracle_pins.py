@@ -535,3 +535,69 @@ def test_backprojection_reproduces_an_in_subspace_decay():
     maps = np.ones((1, 1, ny, nz), complex)
     got = O.synthesize_te(alpha, maps, phi, list(range(T)))[:, 0]
     assert np.abs(got - xt).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------------
+# pre-processing: calibration average, coil compression, readout decoupling, projection
+# ----------------------------------------------------------------------------------
+def _sparse_from_full(rng, yfull, mask):
+    """Sparse readout lines of a full k-space yfull [Ctot][T][Nx][Ny][Nz] at the sampled
+    (t, ky, kz) of mask, in a shuffled order."""
+    t, a, b = np.nonzero(mask)
+    order = rng.permutation(len(t))
+    t, a, b = t[order], a[order], b[order]
+    lines = np.stack([yfull[:, t[j], :, a[j], b[j]] for j in range(len(t))])
+    return lines, t, a, b
+
+
+def test_preprocess_equals_dense_projection_of_decoupled_kspace():
+    """Projection from the sparse lines equals Phi^T P applied to the readout-decoupled
+    dense k-space; the readout transform is checked against the centred DFT matrix."""
+    rng = np.random.default_rng(20)
+    Ctot, C, T, K, nx, ny, nz = 5, 3, 10, 3, 12, 10, 8
+    phi = synth.t2_basis(T, K)
+    mask = (rng.random((T, ny, nz)) < 0.3).astype(np.uint8)
+    yfull = crandn(rng, Ctot, T, nx, ny, nz) * mask[None, :, None]
+    lines, t, a, b = _sparse_from_full(rng, yfull, mask)
+    W = np.linalg.qr(crandn(rng, Ctot, C))[0]
+    ytil, m2 = O.preprocess(lines, t, a, b, W, phi, ny, nz)
+    assert np.array_equal(m2, mask)
+    Dx = centred_dft_matrix(nx)
+    yv = np.einsum("ctxyz,cd->dtxyz", yfull, W)
+    xdec = np.einsum("xk,dtkyz->dtxyz", Dx.conj().T, yv)          # centred unitary IDFT along x
+    ref = np.einsum("tk,dtxyz->xdkyz", phi, xdec * mask[None, :, None])
+    assert np.abs(ytil - ref).max() < 1e-12
+
+
+def test_compression_is_lossless_for_data_in_a_coil_subspace():
+    """Calibration data spanning a C-dimensional channel subspace: the compression matrix
+    is orthonormal, spans that subspace, orders by energy and keeps all of the data."""
+    rng = np.random.default_rng(21)
+    Ctot, C, w = 8, 3, 6
+    B = crandn(rng, C, Ctot)
+    Z = crandn(rng, w ** 3, C) * np.array([3.0, 2.0, 1.0])
+    cal = (Z @ B).T.reshape(Ctot, w, w, w)
+    W = O.compression_matrix(cal, C)
+    assert np.abs(W.conj().T @ W - np.eye(C)).max() < 1e-12
+    X = cal.reshape(Ctot, -1).T
+    assert np.linalg.norm(X - X @ W @ W.conj().T) < 1e-10 * np.linalg.norm(X)
+    energy = np.linalg.norm(X @ W, axis=0)
+    assert np.all(np.diff(energy) < 0)
+    i = np.argmax(np.abs(W), axis=0)
+    assert np.all(np.abs(W[i, range(C)].imag) < 1e-15) and np.all(W[i, range(C)].real > 0)
+
+
+def test_calibration_average_over_echoes():
+    """Two echoes sampling the same central (ky, kz) are averaged; a line outside the
+    window is ignored; an unsampled window point stays zero."""
+    Ctot, nx, ny, nz, w = 2, 8, 8, 8, 4
+    lines = np.zeros((3, Ctot, nx), complex)
+    lines[0] = 1.0
+    lines[1] = 3.0
+    lines[2] = 100.0
+    ky = [4, 4, 0]
+    kz = [5, 5, 0]
+    cal = O.calibration_average(lines, ky, kz, ny, nz, w)
+    assert cal.shape == (Ctot, w, w, w)
+    assert np.all(cal[:, :, 2, 3] == 2.0)        # (ky, kz) = (4, 5) -> window (2, 3)
+    assert np.count_nonzero(cal) == Ctot * w      # only that point, all w kx samples
