@@ -206,6 +206,47 @@ t2sh_status t2sh_postprocess(t2sh_plan_t plan, const void* alpha, const int32_t*
                              void* out);
 
 /*
+ * Pre-processing (Sec. III.A): from the acquisition as a sparse array of fully sampled
+ * readout lines to the projected k-space and masks the solve takes.  Line j (of nlines)
+ * holds the channels [nchan][nx] of phase encode (ky[j], kz[j]) at echo t[j]; every axis
+ * has its DC sample at index n/2.  The index arrays are host memory (read during the
+ * call); line data and results are device memory.  Both calls are plan-free; their
+ * scratch is allocated and freed in stream order on `stream`.
+ */
+typedef struct {
+  int32_t nlines, nchan, nx, ny, nz, nechoes;
+  const int32_t* t;   /* host [nlines], 0 <= t < nechoes  */
+  const int32_t* ky;  /* host [nlines], 0 <= ky < ny      */
+  const int32_t* kz;  /* host [nlines], 0 <= kz < nz      */
+} t2sh_sparse;
+
+/*
+ * t2sh_coil_compression -- Re-sort and Average plus Coil Compression: the central
+ * window^3 k-space block of every channel, each (ky, kz) averaged over the echoes that
+ * sampled it, as calibration rows X [points][nchan]; W [nchan][ncomp] = eigenvectors of
+ * X^H X (right singular vectors of X) by decreasing eigenvalue, each column turned so that
+ * its entry of largest magnitude (first such) is real positive (SVD compression, Zhang et
+ * al. 2013).  lines: device [nlines][nchan][nx] complex64; w_out: device [nchan][ncomp]
+ * complex64.  nchan <= 32, 1 <= ncomp <= nchan, 1 <= window <= min(nx, ny, nz).
+ * Synchronises the stream (to report a non-converged eigensolve as T2SH_ECUDA).
+ */
+t2sh_status t2sh_coil_compression(const t2sh_sparse* sp, const void* lines, int32_t window, int32_t ncomp,
+                                  void* w_out, void* stream);
+
+/*
+ * t2sh_preprocess -- Coil compression applied (y_v = y W), the readout slices decoupled
+ * by the centred unitary 1D inverse DFT along x (Sec. III.B), Re-Sort and Project Data and
+ * Compute Mask: ytil[x][c][k][ky][kz] = sum over lines j at (ky, kz) of phi[t_j][k]
+ * yhat_j[c][x] (lines repeating (t, ky, kz) add), mask[t][ky][kz] = 1 where sampled.
+ * ytil_out: device [nx][ncomp][nbasis][ny][nz] complex64 = the projected k-space of nx
+ * slices as t2sh_solve takes it (kform T2SH_KSPACE_PROJ); mask_out: device [nechoes][ny][nz].
+ * phi: device [nechoes][nbasis] float.  nx even, a product of 2, 3, 5 and 13.
+ * Asynchronous on `stream`.
+ */
+t2sh_status t2sh_preprocess(const t2sh_sparse* sp, const void* lines, const void* w, int32_t ncomp, const float* phi,
+                            int32_t nbasis, void* ytil_out, uint8_t* mask_out, void* stream);
+
+/*
  * Resumable solve, for schedulers that interleave several scans (t2sh_solve is
  * t2sh_solve_begin + t2sh_solve_iterate(dims.iters) + t2sh_solve_end):
  *   t2sh_solve_begin    forms A^H y from the k-space (as t2sh_solve) and resets the FISTA

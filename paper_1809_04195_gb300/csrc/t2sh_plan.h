@@ -17,6 +17,7 @@ constexpr int kMaxK = 8;
 constexpr int kMaxM = 2;
 constexpr int kMaxBlock = 16;
 constexpr int kMaxPostTe = 8;                    // echoes one t2sh_postprocess call synthesises
+constexpr int kMaxChan = 32;                     // receive channels of the coil-compression step
 
 // Radix plan of a length-n FFT: pass q has radix radix[q] and ns[q] = prod of the
 // radices of passes 0..q-1 (Stockham autosort).
@@ -90,6 +91,18 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
 size_t post_smem_bytes(const Geom& g, int nte);
 cudaError_t launch_post(const Geom& g, const FftPlan& pz, const float2* tw_z, const float2* maps, const float* phi,
                         const float2* alpha, const int* te, int nte, int w, float* out, cudaStream_t st);
+// pre-processing from sparse readout lines (k_preproc.cu)
+cudaError_t launch_calib(const float2* lines, int ctot, int nx, const int* order, const int* seg_off, const int* wseg,
+                         int nwseg, int win, float2* X, cudaStream_t st);
+cudaError_t launch_gram_eig(const float2* X, long long npts, int ctot, int ncomp, double* G, float2* W, int* err,
+                            cudaStream_t st);
+cudaError_t launch_compress_readout(const float2* lines, const float2* W, int nlines, int ctot, int ncomp,
+                                    const FftPlan& px, const float2* tw_x, float2* yh, cudaStream_t st);
+cudaError_t launch_project_lines(const float2* yh, int ncomp, int nx, const int* order, const int* tj,
+                                 const int* seg_off, const int* seg_y, const int* seg_z, int nseg, const float* phi,
+                                 int K, int ny, int nz, float2* ytil, cudaStream_t st);
+cudaError_t launch_mark_mask(const int* t, const int* ky, const int* kz, int n, int ny, int nz, uint8_t* mask,
+                             cudaStream_t st);
 // ADMM v-update: w = alpha + u, v = LLR prox of w (threshold a.tau, shift a.sy/a.sz), u <- w - v
 cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alpha, float2* v, float2* u,
                             cudaStream_t st);

@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
             "t2sh_solve": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
             "t2sh_solve_admm": [_vp, _vp, _i32, _vp, _f32, _i32, ctypes.POINTER(ctypes.c_double)],
             "t2sh_postprocess": [_vp, _vp, ctypes.POINTER(_i32), _i32, _f32, _vp],
+            "t2sh_coil_compression": [ctypes.POINTER(Sparse), _vp, _i32, _i32, _vp, _vp],
+            "t2sh_preprocess": [ctypes.POINTER(Sparse), _vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp],
             "t2sh_get_step": [_vp, ctypes.POINTER(_f32)],
             "t2sh_shifts": [_u64, _i32, _i32, ctypes.POINTER(_i32)],
             "t2sh_workspace_bytes": [ctypes.POINTER(Dims), ctypes.POINTER(ctypes.c_size_t)],
@@ -142,6 +144,57 @@ def _ptr(t, dtype, shape, host: bool):
     if host == t.is_cuda:
         raise ValueError("host_io plans take host arrays; other plans take CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
+
+
+class Sparse(ctypes.Structure):
+    """t2sh_sparse: the acquisition as readout lines (index arrays in host memory)."""
+    _fields_ = [("nlines", ctypes.c_int32), ("nchan", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("nechoes", ctypes.c_int32),
+                ("t", ctypes.POINTER(ctypes.c_int32)), ("ky", ctypes.POINTER(ctypes.c_int32)),
+                ("kz", ctypes.POINTER(ctypes.c_int32))]
+
+
+def _sparse(lines, t, ky, kz, ny, nz, nechoes):
+    keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (t, ky, kz)]
+    n, nchan, nx = (int(v) for v in lines.shape)
+    if any(len(a) != n for a in keep):
+        raise ValueError("t, ky, kz need one entry per line")
+    ptr = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for a in keep]
+    return Sparse(n, nchan, nx, int(ny), int(nz), int(nechoes), *ptr), keep
+
+
+def coil_compression(lines, t, ky, kz, ny: int, nz: int, nechoes: int, window: int = 24, ncomp: int = 7,
+                     stream=None):
+    """Compression matrix W [nchan][ncomp] (device) from the central window of the sparse
+    readout lines (device [nlines][nchan][nx] complex64); t, ky, kz: host index arrays."""
+    import torch
+    sp, keep = _sparse(lines, t, ky, kz, ny, nz, nechoes)
+    w = torch.empty((int(lines.shape[1]), int(ncomp)), dtype=torch.complex64, device="cuda")
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().t2sh_coil_compression(ctypes.byref(sp), _ptr(lines, torch.complex64, tuple(lines.shape), False),
+                                       int(window), int(ncomp), ctypes.c_void_p(w.data_ptr()),
+                                       ctypes.c_void_p(st.cuda_stream)))
+    del keep
+    return w
+
+
+def preprocess(lines, t, ky, kz, w, phi, ny: int, nz: int, stream=None):
+    """(ytil [nx][ncomp][K][ny][nz] complex64, mask [T][ny][nz] uint8), device: coil
+    compression with w, readout decoupling, re-sort and projection onto phi [T][K]."""
+    import torch
+    T, K = (int(v) for v in phi.shape)
+    sp, keep = _sparse(lines, t, ky, kz, ny, nz, T)
+    ncomp = int(w.shape[1])
+    nx = int(lines.shape[2])
+    ytil = torch.empty((nx, ncomp, K, int(ny), int(nz)), dtype=torch.complex64, device="cuda")
+    mask = torch.empty((T, int(ny), int(nz)), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().t2sh_preprocess(ctypes.byref(sp), _ptr(lines, torch.complex64, tuple(lines.shape), False),
+                                 _ptr(w, torch.complex64, tuple(w.shape), False), ncomp,
+                                 _ptr(phi, torch.float32, (T, K), False), K, ctypes.c_void_p(ytil.data_ptr()),
+                                 ctypes.c_void_p(mask.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+    del keep
+    return ytil, mask
 
 
 def normal_op_noalloc(dims: Dims, phi, mask, maps, x, out=None, stream=None):
