@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--cg-iters", type=int, default=3)
     ap.add_argument("--post-te", default="",
                     help="comma-separated echo indices: each step also forms TE images (t2sh_postprocess, pf 0.65)")
+    ap.add_argument("--preproc", action="store_true",
+                    help="time the pre-processing instead (coil compression 16 -> C channels and sparse lines -> "
+                         "projected k-space for the whole scan); prints its own JSON line")
     ap.add_argument("--workload", choices=["knee", "paper"], default="knee",
                     help="paper: the Table I scan (288 slices of 260x240, C=7, M=2, b=12, 250 iterations)")
     return ap.parse_args()
@@ -390,8 +393,59 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_preproc(args):
+    """Seconds per scan of t2sh_coil_compression + t2sh_preprocess on a synthetic sparse
+    acquisition of the workload: the scan's per-echo masks, one fully sampled readout line
+    of nx = slices samples for every (t, ky, kz) sampled, 16 receive channels compressed
+    to the scan's C virtual channels (24^3 calibration window), random line data."""
+    import numpy as np
+    import torch
+    import t2sh_synth as synth
+    from paper_1809_04195_gb300 import build as B
+    B.build()
+    from paper_1809_04195_gb300 import t2sh
+    sh, S, _ = workload(args)
+    dev = torch.device("cuda", 0)
+    phi, mask, _ = synth.scan_common(sh)
+    t, a, b = (v.astype(np.int32) for v in np.nonzero(mask))
+    nchan, nx = 16, S
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(sh.seed)
+    lines = torch.randn((len(t), nchan, nx), dtype=torch.complex64, device=dev, generator=gen)
+    phi_d = torch.from_numpy(phi.astype(np.float32)).to(dev)
+
+    def step():
+        w = t2sh.coil_compression(lines, t, a, b, sh.ny, sh.nz, sh.nechoes, window=24, ncomp=sh.ncoils)
+        return t2sh.preprocess(lines, t, a, b, w, phi_d, sh.ny, sh.nz)
+
+    for _ in range(args.warmup):
+        out = step()
+    del out
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        out = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    in_bytes = lines.numel() * 8
+    out_bytes = out[0].numel() * 8 + out[1].numel()
+    print(json.dumps({"metric": "pre-processing seconds per scan (coil compression + sparse lines to projected "
+                                "k-space)", "value": ms / 1000.0, "unit": "s", "higher_is_better": False,
+                      "steps": args.steps, "warmup": args.warmup, "n_gpus": 1, "dtype": "f32",
+                      "data": "synthetic (random line data at the scan's sampling pattern)",
+                      "config": {"workload": config_dict(sh, S, sh.iters, 1)["workload"], "lines": int(len(t)),
+                                 "channels": nchan, "virtual_channels": sh.ncoils, "nx": nx,
+                                 "line_bytes": int(in_bytes), "projected_bytes": int(out_bytes)},
+                      "achieved_gbs_in_plus_out": (in_bytes + out_bytes) / (ms / 1000.0) / 1e9}), flush=True)
+
+
 def main():
     args = parse()
+    if args.preproc:
+        run_preproc(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
