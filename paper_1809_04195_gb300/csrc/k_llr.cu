@@ -27,7 +27,9 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
           const float2* __restrict__ aty, float2* u) {
   constexpr bool FISTA = MODE == LLR_FISTA;
   extern __shared__ float2 smem[];
-  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, M = g.M, b = a.b;
+  // one CTA per (band, slice, map set): the blocks of different map sets are independent
+  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, b = a.b;
+  const int M = 1, MS = g.M, m0 = blockIdx.z;  // map sets staged by this CTA, total, this one
   const int s = blockIdx.y, band = blockIdx.x;
   const int rb = min(b, ny - band * b);
   const int nbz = (nz + b - 1) / b;
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
     const int r = rest % rb;
     rest /= rb;  // m * K + k
     const int y = (a.sy + band * b + r) % ny;
-    const long long gi = ((long long)s * M * K + rest) * N + (long long)y * nz + zz;
+    const long long gi = (((long long)s * MS + m0) * K + rest) * N + (long long)y * nz + zz;
     float4 v;
     if (MODE == LLR_ADMM) {
       const float4 av = *reinterpret_cast<const float4*>(x + gi);
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
     float2 xv[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[((m * K + k) * rb + r) * nz + zz] : make_float2(0.f, 0.f);
-    const long long gb = ((long long)(s * M + m) * K) * N + (long long)y * nz + zz;
+    const long long gb = ((long long)(s * MS + m0 + m) * K) * N + (long long)y * nz + zz;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       if (k < K) {
@@ -176,8 +178,8 @@ template <int KC, int MODE, typename ET>
 static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                           const float2* aty, float2* u, cudaStream_t st) {
   const int nbz = (g.nz + a.b - 1) / a.b;
-  const int nblk = g.M * nbz;
-  const size_t sm = sizeof(float2) * ((size_t)g.M * g.K * a.b * g.nz + (size_t)nblk * KC * KC) +
+  const int nblk = nbz;  // per map set
+  const size_t sm = sizeof(float2) * ((size_t)g.K * a.b * g.nz + (size_t)nblk * KC * KC) +
                     sizeof(float) * (size_t)nblk * KC * KC;
   static bool attr = false;
   if (!attr) {
@@ -185,7 +187,7 @@ static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* 
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid((g.ny + a.b - 1) / a.b, g.S);
+  dim3 grid((g.ny + a.b - 1) / a.b, g.S, g.M);
   k_llr<KC, MODE, ET><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty, u);
   return cudaGetLastError();
 }
@@ -213,8 +215,8 @@ cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alp
 
 size_t llr_smem_bytes(const Geom& g, int b) {
   const int kc = g.K <= 4 ? 4 : 8;
-  const int nblk = g.M * ((g.nz + b - 1) / b);
-  return sizeof(float2) * ((size_t)g.M * g.K * b * g.nz + (size_t)nblk * kc * kc) + sizeof(float) * (size_t)nblk * kc * kc;
+  const int nblk = (g.nz + b - 1) / b;  // one map set per CTA
+  return sizeof(float2) * ((size_t)g.K * b * g.nz + (size_t)nblk * kc * kc) + sizeof(float) * (size_t)nblk * kc * kc;
 }
 
 }  // namespace t2sh

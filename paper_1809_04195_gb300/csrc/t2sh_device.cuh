@@ -119,34 +119,43 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[7] = csub(e[3], o3);
 }
 
+// 16 = 4 x 4 Cooley-Tukey: DFT_4 over n1 of x[4 n1 + n2] for each n2, twiddles
+// w16^(n2 k1), DFT_4 over n2 -> X[k1 + 4 k2].  w16^4 = -+i is a swap; the others are
+// constant complex multiplies (cos and sin of m pi / 8 written out).
+template <bool INV>
+__device__ __forceinline__ float2 cmul_cs(float2 v, float c, float s) {  // v * (c -+ i s)
+  const float si = INV ? s : -s;
+  return make_float2(v.x * c - v.y * si, v.x * si + v.y * c);
+}
 template <bool INV>
 __device__ __forceinline__ void dft16(float2* v) {
-  // w16^k = cos(pi k / 8) -+ i sin(pi k / 8)
-  const float C[8] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-                      0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f};
-  const float S[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
-                      1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
-  float2 e[8], o[8];
+  constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  float2 a[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    e[i] = v[2 * i];
-    o[i] = v[2 * i + 1];
+  for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) a[n2][n1] = v[4 * n1 + n2];
+    dft4<INV>(a[n2]);
   }
-  dft8<INV>(e);
-  dft8<INV>(o);
+  // a[n2][k1] *= w16^(n2 k1), w16^m = cos(m pi / 8) -+ i sin(m pi / 8)
+  a[1][1] = cmul_cs<INV>(a[1][1], c1, s1);   // m = 1
+  a[1][2] = cmul_cs<INV>(a[1][2], h, h);     // m = 2
+  a[1][3] = cmul_cs<INV>(a[1][3], s1, c1);   // m = 3
+  a[2][1] = cmul_cs<INV>(a[2][1], h, h);     // m = 2
+  a[2][2] = rot_i<INV>(a[2][2]);             // m = 4
+  a[2][3] = cmul_cs<INV>(a[2][3], -h, h);    // m = 6
+  a[3][1] = cmul_cs<INV>(a[3][1], s1, c1);   // m = 3
+  a[3][2] = cmul_cs<INV>(a[3][2], -h, h);    // m = 6
+  a[3][3] = cmul_cs<INV>(a[3][3], -c1, -s1); // m = 9
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    float2 w = make_float2(C[k], INV ? S[k] : -S[k]);
-    float2 t = cmul(o[k], w);
-    v[k] = cadd(e[k], t);
-    v[k + 8] = csub(e[k], t);
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
   }
 }
 
-// Good-Thomas (prime factor) DFT of length A*B with gcd(A, B) = 1: with input map
-// n = (B n1 + A n2) mod AB and output map k = (B eA k1 + A eB k2) mod AB, where
-// eA = B^-1 mod A and eB = A^-1 mod B, the length-AB DFT is a 2D A x B DFT with no
-// twiddle factors.  Every index is a compile-time constant.
 // 13-point DFT through the pair symmetry of the kernel: with u_n = x_n + x_(13-n) and
 // w_n = x_n - x_(13-n) (n = 1..6), X_k = x_0 + sum_n cos(2 pi n k / 13) u_n -+ i sum_n
 // sin(2 pi n k / 13) w_n and X_(13-k) the same with the other sign (k = 1..6).  The
@@ -189,6 +198,10 @@ __device__ __forceinline__ void dft13(float2* v) {
   }
 }
 
+// Good-Thomas (prime factor) DFT of length A*B with gcd(A, B) = 1: with input map
+// n = (B n1 + A n2) mod AB and output map k = (B eA k1 + A eB k2) mod AB, where
+// eA = B^-1 mod A and eB = A^-1 mod B, the length-AB DFT is a 2D A x B DFT with no
+// twiddle factors.  Every index is a compile-time constant.
 constexpr int inv_mod(int a, int m) {
   for (int x = 1; x < m; ++x)
     if ((a * x) % m == 1) return x;
