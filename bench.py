@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "slice-iterations/s (T2 Shuffling FISTA PICS solve, full scan)"
 UNIT = "slice-iter/s"
-KERNEL_FILES = ["t2sh_device.cuh", "t2sh_plan.h", "k_fft.cu", "k_fft_fast.cu", "k_col_tma.cu", "k_fused.cu", "k_llr.cu",
+KERNEL_FILES = ["t2sh_device.cuh", "t2sh_plan.h", "k_fft.cu", "k_fft_fast.cu", "k_col_tma.cu", "k_col_pr.cu", "k_fused.cu", "k_llr.cu",
                 "k_prep.cu", "t2sh_api.cu"]
 
 

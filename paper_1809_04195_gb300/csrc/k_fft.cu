@@ -482,6 +482,8 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
       {
         const cudaError_t ef = launch_col_normal_fast(g, tw_y, psi, tout, st);
         if (ef != cudaErrorNotSupported) return ef;
+        const cudaError_t ep = launch_col_normal_pr(g, tw_y, psi, tout, st);
+        if (ep != cudaErrorNotSupported) return ep;
       }
       return k4 ? col_normal_go<4>(g, py, tw_y, psi, tout, st) : col_normal_go<8>(g, py, tw_y, psi, tout, st);
     case COL_ADJ_DATA:

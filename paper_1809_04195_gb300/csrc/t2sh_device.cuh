@@ -246,6 +246,7 @@ __device__ __forceinline__ void dft_r(float2* v) {
   else if constexpr (R == 13) dft13<INV>(v);
   else if constexpr (R == 15) dft_pfa<3, 5, INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
+  else if constexpr (R == 20) dft_pfa<4, 5, INV>(v);
   else static_assert(R == 2, "unsupported radix");
 }
 
