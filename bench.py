@@ -325,18 +325,28 @@ def run_ours(args):
         hd = t2sh.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=sh.nmaps, block=sh.block,
                             lam=sh.lam, iters=iters, seed=sh.seed, precision=prec, flags=t2sh.HOST_IO)
 
+        phases = [0.0, 0.0, 0.0]  # plan, solve (host buffers in and out), destroy
+
         def hstep():
+            t0 = time.perf_counter()
             p = t2sh.Plan(hd, hphi, hmask, hmaps)
+            t1 = time.perf_counter()
             if args.solver == "admm":
                 p.solve_admm(hy, t2sh.KSPACE_PROJ, rho=args.rho, cg_iters=args.cg_iters, out=hout)
             else:
                 p.solve(hy, t2sh.KSPACE_PROJ, out=hout)
+            t2 = time.perf_counter()
             p.close()
+            t3 = time.perf_counter()
+            phases[0] += t1 - t0
+            phases[1] += t2 - t1
+            phases[2] += t3 - t2
 
         hstep()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        phases[:] = [0.0, 0.0, 0.0]
         e0 = time.perf_counter()
         for _ in range(args.steps):
             hstep()
@@ -345,7 +355,9 @@ def run_ours(args):
         h2d = hphi.nbytes + hmask.nbytes + hmaps.numel() * 8 + hy.numel() * 8
         e2e = {"value": sum_over_ranks(units * args.steps) / es, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hout.numel() * 8), "full_scan_s": es / args.steps,
-               "api": "t2sh_plan + t2sh_solve with T2SH_HOST_IO (pinned host buffers)"}
+               "api": "t2sh_plan + t2sh_solve with T2SH_HOST_IO (pinned host buffers)",
+               "ms_per_step": {"plan": 1000 * phases[0] / args.steps, "solve": 1000 * phases[1] / args.steps,
+                               "destroy": 1000 * phases[2] / args.steps}}
         del hmaps, hy, hout
 
     if rank != 0:

@@ -1,6 +1,7 @@
 // Host runtime behind the C ABI of include/t2sh.h: argument validation, the plan's
 // device workspace, plan-time precomputation (Psi, sign-folded maps, step, shift
 // table) and the FISTA driver that enqueues the kernels of each iteration.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -50,6 +51,32 @@ void set_err(const char* fmt, ...) {
       return T2SH_EINVAL;          \
     }                              \
   } while (0)
+
+// Stream-ordered pool for the host-IO k-space stage, one per device, keeping its memory
+// (release threshold at the maximum) so that plans made one after another reuse it.
+cudaMemPool_t stage_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
 
 // SplitMix64 (Steele, Lea & Flood 2014): output number i+1 of the stream from `seed`.
 uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
@@ -166,7 +193,9 @@ struct t2sh_plan_s {
   float2* t = nullptr;
   double* res = nullptr;
   unsigned* red = nullptr;
-  void* stage = nullptr;  // host-IO staging of k-space input
+  void* stage = nullptr;  // host-IO staging of k-space input (from stage_pool(), stream-ordered)
+  cudaStream_t cs = nullptr;           // copy stream of the pipelined host-IO solve
+  std::vector<cudaEvent_t> cev;        // its events
   size_t stage_bytes = 0;
   std::vector<int32_t> shifts;
   float mu = 1.f;
@@ -205,6 +234,8 @@ struct t2sh_plan_s {
     return T2SH_OK;
   }
   ~t2sh_plan_s() {
+    for (cudaEvent_t e : cev) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
     for (void* p : allocs) cudaFree(p);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
@@ -400,7 +431,10 @@ t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* ma
 t2sh_status t2sh_destroy(t2sh_plan_t p) {
   if (!p) return T2SH_OK;
   cudaStreamSynchronize(p->st);
-  if (p->stage) cudaFree(p->stage);
+  if (p->stage) {
+    cudaFreeAsync(p->stage, p->st);
+    cudaStreamSynchronize(p->st);
+  }
   delete p;
   return T2SH_OK;
 }
@@ -497,6 +531,25 @@ t2sh_status t2sh_llr_prox(t2sh_plan_t p, void* x, float tau, int32_t sy, int32_t
 
 namespace {
 
+// The host-IO stage of at least kb bytes, allocated in stream order on the plan's stream
+// from the stage pool (the default pool if that is unavailable).
+t2sh_status ensure_stage(t2sh_plan_t p, size_t kb) {
+  if (p->stage_bytes >= kb) return T2SH_OK;
+  if (p->stage) cudaFreeAsync(p->stage, p->st);
+  p->stage = nullptr;
+  p->stage_bytes = 0;
+  cudaMemPool_t pool = stage_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p->stage, kb, pool, p->st) : cudaMallocAsync(&p->stage, kb, p->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->stage = nullptr;
+    set_err("allocation of %zu bytes for the k-space stage failed", kb);
+    return T2SH_ENOMEM;
+  }
+  p->stage_bytes = kb;
+  return T2SH_OK;
+}
+
 // A^H y from the k-space (staged through the plan with T2SH_HOST_IO) and a fresh FISTA state.
 t2sh_status begin_impl(t2sh_plan_t p, const void* kspace, int32_t kform, bool record_res) {
   T2SH_REQ(p && kspace, "NULL argument");
@@ -506,17 +559,8 @@ t2sh_status begin_impl(t2sh_plan_t p, const void* kspace, int32_t kform, bool re
   const void* ky = kspace;
   if (p->host_io) {
     const size_t kb = kspace_bytes(d, kform);
-    if (p->stage_bytes < kb) {
-      if (p->stage) cudaFree(p->stage);
-      p->stage = nullptr;
-      p->stage_bytes = 0;
-      if (cudaMalloc(&p->stage, kb) != cudaSuccess) {
-        cudaGetLastError();
-        set_err("cudaMalloc(%zu) for the k-space stage failed", kb);
-        return T2SH_ENOMEM;
-      }
-      p->stage_bytes = kb;
-    }
+    t2sh_status se = ensure_stage(p, kb);
+    if (se != T2SH_OK) return se;
     T2SH_CK(cudaMemcpyAsync(p->stage, kspace, kb, cudaMemcpyHostToDevice, p->st));
     ky = p->stage;
   }
@@ -535,7 +579,7 @@ t2sh_status begin_impl(t2sh_plan_t p, const void* kspace, int32_t kform, bool re
 // One FISTA iteration (index p->iter_done) of Eq. 5.
 t2sh_status iteration(t2sh_plan_t p) {
   const t2sh_dims& d = p->d;
-  const size_t vec = footprint(d).vec;
+  const size_t vec = cbytes((long long)p->g.S * p->g.M * p->g.K * p->g.ny * p->g.nz);  // slices in view
   const int it = p->iter_done;
   const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * p->tk * p->tk));
   FistaArgs a{};
@@ -604,12 +648,106 @@ t2sh_status end_impl(t2sh_plan_t p, void* alpha_out, double* residual_out, const
   return T2SH_OK;
 }
 
+// The plan's per-slice buffers seen as the slices [s0, s0 + n) only; restores the full view.
+struct SliceView {
+  t2sh_plan_t p;
+  Geom g;
+  float2 *x, *z, *aty, *grad, *maps;
+  SliceView(t2sh_plan_t p_, int s0, int n) : p(p_), g(p_->g), x(p_->x), z(p_->z), aty(p_->aty), grad(p_->grad), maps(p_->maps) {
+    const long long N = (long long)g.ny * g.nz;
+    const long long vs = (long long)g.M * g.K * N, ms = (long long)g.C * g.M * N;
+    p->g.S = n;
+    p->x += s0 * vs; p->z += s0 * vs; p->aty += s0 * vs; p->grad += s0 * vs; p->maps += s0 * ms;
+  }
+  ~SliceView() {
+    p->g = g; p->x = x; p->z = z; p->aty = aty; p->grad = grad; p->maps = maps;
+  }
+};
+
+constexpr int kHostChunks = 2;
+
+// One-shot solve through host buffers (T2SH_HOST_IO).  Slices are independent and every
+// slice runs the same shift and momentum sequence, so the scan is solved in two chunks of
+// slices: a small first one (an eighth) whose copy alone is waited for, and the rest, whose
+// k-space crosses on a copy stream while the first chunk is solved.  Each chunk's result
+// is copied back on the copy stream (the first one's while the second is solved).
+t2sh_status solve_host_pipelined(t2sh_plan_t p, const void* kspace, int32_t kform, void* alpha_out,
+                                 double* residual_out) {
+  T2SH_REQ(p && kspace && alpha_out, "NULL argument");
+  T2SH_REQ(kform == T2SH_KSPACE_TE || kform == T2SH_KSPACE_PROJ, "bad kform %d", kform);
+  const t2sh_dims& d = p->d;
+  const int S = d.nslices;
+  const int first = std::max(1, S / 8);
+  const int bounds[kHostChunks + 1] = {0, first, S};
+  const int nch = kHostChunks;
+  const size_t kb = kspace_bytes(d, kform), kbs = kb / S;
+  const size_t vslice = footprint(d).vec / S;
+  {
+    t2sh_status se = ensure_stage(p, kb);
+    if (se != T2SH_OK) return se;
+  }
+  if (!p->cs) T2SH_CK(cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking));
+  while ((int)p->cev.size() < 2 * kHostChunks + 2) {
+    cudaEvent_t e;
+    T2SH_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    p->cev.push_back(e);
+  }
+  cudaEvent_t* ev_in = p->cev.data();
+  cudaEvent_t* ev_out = ev_in + kHostChunks;
+  cudaEvent_t ev_start = p->cev[2 * kHostChunks], ev_done = p->cev[2 * kHostChunks + 1];
+  // the copies must not overwrite the stage under work already queued on the plan's stream
+  T2SH_CK(cudaEventRecord(ev_start, p->st));
+  T2SH_CK(cudaStreamWaitEvent(p->cs, ev_start, 0));
+  char* stage = static_cast<char*>(p->stage);
+  const char* src = static_cast<const char*>(kspace);
+  for (int c = 0; c < nch; ++c) {
+    const int s0 = bounds[c], n = bounds[c + 1] - s0;
+    T2SH_CK(cudaMemcpyAsync(stage + s0 * kbs, src + s0 * kbs, n * kbs, cudaMemcpyHostToDevice, p->cs));
+    T2SH_CK(cudaEventRecord(ev_in[c], p->cs));
+  }
+  const bool rec = residual_out != nullptr;
+  if (rec && d.iters > 0) T2SH_CK(cudaMemsetAsync(p->res, 0, sizeof(double) * 2 * (size_t)d.iters, p->st));
+  char* out = static_cast<char*>(alpha_out);
+  for (int c = 0; c < nch; ++c) {
+    const int s0 = bounds[c], n = bounds[c + 1] - s0;
+    T2SH_CK(cudaStreamWaitEvent(p->st, ev_in[c], 0));
+    {
+      SliceView view(p, s0, n);
+      t2sh_status s = adjoint_data(p, stage + s0 * kbs, kform, p->aty);
+      if (s != T2SH_OK) return s;
+      T2SH_CK(cudaMemsetAsync(p->x, 0, n * vslice, p->st));
+      T2SH_CK(cudaMemsetAsync(p->z, 0, n * vslice, p->st));
+      p->begun = true;
+      p->iter_done = 0;
+      p->tk = 1.0;
+      p->record_res = rec;
+      s = iterate_impl(p, d.iters);
+      if (s != T2SH_OK) return s;
+      T2SH_CK(cudaEventRecord(ev_out[c], p->st));
+      T2SH_CK(cudaStreamWaitEvent(p->cs, ev_out[c], 0));
+      T2SH_CK(cudaMemcpyAsync(out + s0 * vslice, p->x, n * vslice, cudaMemcpyDeviceToHost, p->cs));
+    }
+  }
+  T2SH_CK(cudaEventRecord(ev_done, p->cs));
+  T2SH_CK(cudaStreamWaitEvent(p->st, ev_done, 0));
+  if (rec && d.iters > 0) {
+    std::vector<double> r(2 * (size_t)d.iters);
+    T2SH_CK(cudaMemcpyAsync(r.data(), p->res, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, p->st));
+    T2SH_CK(cudaStreamSynchronize(p->st));
+    for (int it = 0; it < d.iters; ++it) residual_out[it] = r[2 * it + 1] > 0.0 ? std::sqrt(r[2 * it] / r[2 * it + 1]) : 0.0;
+  } else {
+    T2SH_CK(cudaStreamSynchronize(p->st));
+  }
+  return T2SH_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 t2sh_status t2sh_solve(t2sh_plan_t p, const void* kspace, int32_t kform, void* alpha_out, double* residual_out) {
   T2SH_REQ(p && kspace && alpha_out, "NULL argument");
+  if (p->host_io && p->d.nslices > 1) return solve_host_pipelined(p, kspace, kform, alpha_out, residual_out);
   t2sh_status s = begin_impl(p, kspace, kform, residual_out != nullptr);
   if (s == T2SH_OK) s = iterate_impl(p, p->d.iters);
   if (s == T2SH_OK) s = end_impl(p, alpha_out, residual_out);
