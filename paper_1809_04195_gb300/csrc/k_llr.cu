@@ -2,59 +2,67 @@
 // as Sec. IV.C describes: the random circular shift is folded into the gather
 // indices (no shifted copy), each block is thresholded on chip and written back.
 //
-// One CTA per (slice, band of b shifted rows).  Per block (b x b pixels x K, per map
-// set) a warp forms the K x K Gram matrix G = X^H X with shuffle reductions; one
-// thread per block then eigendecomposes G = V diag(lambda) V^H (cyclic Jacobi, float32
-// by default, float64 on request), sigma_i = sqrt(lambda_i), and forms
-// W = V diag(max(1 - tau/sigma_i, 0)) V^H,
-// so that X W = U max(Sigma - tau, 0) V^H (since X V = U Sigma).  The FISTA variant
-// fuses the gradient step before the prox and the momentum update after it (Sec. II.A);
-// the ADMM variant thresholds alpha + u and writes v and the scaled dual u + alpha - v.
+// Work unit = (slice, map set, band of b shifted rows); the blocks of different map sets
+// are independent.  Per unit: gather the band into shared memory; per block (b x b
+// pixels x K) a warp forms the K x K Gram matrix G = X^H X with shuffle reductions; one
+// thread per block eigendecomposes G = V diag(lambda) V^H (cyclic Jacobi, float32 by
+// default, float64 on request), sigma_i = sqrt(lambda_i), and forms
+// W = V diag(max(1 - tau/sigma_i, 0)) V^H, so that X W = U max(Sigma - tau, 0) V^H
+// (since X V = U Sigma); then X' = X W is written back.  The FISTA variant fuses the
+// gradient step before the prox and the momentum update after it (Sec. II.A); the ADMM
+// variant thresholds alpha + u and writes v and the scaled dual u + alpha - v.
+//
+// One unit per CTA.  (A persistent schedule with two band buffers, one warp
+// thresholding unit i while the others gather unit i+1, measured slower at the knee
+// shape: its two CTAs per SM hide less memory latency than three single-buffer CTAs.)
+#include <algorithm>
+
 #include "t2sh_device.cuh"
 
 namespace t2sh {
 
 enum { LLR_PROX = 0, LLR_FISTA = 1, LLR_ADMM = 2 };
 
-// The K <= 4 float32 variant is held to 80 registers so that three CTAs share an SM and
-// the single-thread eigen-steps of one band overlap the memory phases of the others.
-// MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
-// z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
-// u <- w - v.
-template <int KC, int MODE, typename ET>
-__global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1)
-    k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
-          const float2* __restrict__ aty, float2* u) {
-  constexpr bool FISTA = MODE == LLR_FISTA;
-  extern __shared__ float2 smem[];
-  // one CTA per (band, slice, map set): the blocks of different map sets are independent
-  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, b = a.b;
-  const int M = 1, MS = g.M, m0 = blockIdx.z;  // map sets staged by this CTA, total, this one
-  const int s = blockIdx.y, band = blockIdx.x;
-  const int rb = min(b, ny - band * b);
-  const int nbz = (nz + b - 1) / b;
-  const int nblk = M * nbz;
-  float2* gs = smem;                                   // [M][K][rb][nz]
-  float2* wm = gs + (size_t)M * K * rb * nz;           // [nblk][KC][KC]
-  float* gram = reinterpret_cast<float*>(wm + (size_t)nblk * KC * KC);  // [nblk][KC*KC]
+namespace {
 
-  // 1. gather the band (gradient step fused for FISTA), two pixels per float4
-  const int nel2 = (M * K * rb * nz) >> 1;
+struct LlrUnit {
+  int s, m0, band, rb;
+};
+
+__device__ __forceinline__ LlrUnit llr_unit(const Geom& g, int b, int unit) {
+  const int nbands = (g.ny + b - 1) / b;
+  LlrUnit un;
+  un.band = unit % nbands;
+  const int sm = unit / nbands;
+  un.m0 = sm % g.M;
+  un.s = sm / g.M;
+  un.rb = min(b, g.ny - un.band * b);
+  return un;
+}
+
+// 1. gather the band into gs [K][rb][nz] (gradient step fused for FISTA), two pixels per
+// float4, threads t0 .. t0 + nth - 1 of the CTA
+template <int MODE>
+__device__ __forceinline__ void llr_gather(const Geom& g, const FistaArgs& a, const LlrUnit& un, float2* gs,
+                                           const float2* x, const float2* z, const float2* __restrict__ grad,
+                                           const float2* __restrict__ aty, const float2* u, int t0, int nth) {
+  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, b = a.b, rb = un.rb;
+  const int nel2 = (K * rb * nz) >> 1;
 #pragma unroll 4
-  for (int e2 = threadIdx.x; e2 < nel2; e2 += kThreads) {
+  for (int e2 = (int)threadIdx.x - t0; e2 < nel2; e2 += nth) {
     const int e = 2 * e2;
     const int zz = e % nz;
     int rest = e / nz;
     const int r = rest % rb;
-    rest /= rb;  // m * K + k
-    const int y = (a.sy + band * b + r) % ny;
-    const long long gi = (((long long)s * MS + m0) * K + rest) * N + (long long)y * nz + zz;
+    rest /= rb;  // k
+    const int y = (a.sy + un.band * b + r) % ny;
+    const long long gi = (((long long)un.s * g.M + un.m0) * K + rest) * N + (long long)y * nz + zz;
     float4 v;
     if (MODE == LLR_ADMM) {
       const float4 av = *reinterpret_cast<const float4*>(x + gi);
       const float4 uv = *reinterpret_cast<const float4*>(u + gi);
       v = make_float4(av.x + uv.x, av.y + uv.y, av.z + uv.z, av.w + uv.w);
-    } else if (FISTA) {
+    } else if (MODE == LLR_FISTA) {
       const float4 zv = *reinterpret_cast<const float4*>(z + gi);
       const float4 gv = *reinterpret_cast<const float4*>(grad + gi);
       const float4 av = *reinterpret_cast<const float4*>(aty + gi);
@@ -66,12 +74,17 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
     gs[e] = make_float2(v.x, v.y);
     gs[e + 1] = make_float2(v.z, v.w);
   }
-  __syncthreads();
+}
 
-  // 2. Gram matrices, one warp per block
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int blk = warp; blk < nblk; blk += kThreads / 32) {
-    const int m = blk / nbz, j = blk - m * nbz;
+// 2. Gram matrices of the band's blocks, one warp per block, warps w0 .. w0 + nw - 1
+template <int KC>
+__device__ __forceinline__ void llr_gram(const Geom& g, const FistaArgs& a, const LlrUnit& un, const float2* gs,
+                                         float* gram, int w0, int nw) {
+  const int nz = g.nz, K = g.K, b = a.b, rb = un.rb;
+  const int nbz = (nz + b - 1) / b;
+  const int warp = (int)(threadIdx.x >> 5) - w0, lane = threadIdx.x & 31;
+  for (int blk = warp; blk < nbz; blk += nw) {
+    const int j = blk;
     const int cb = min(b, nz - j * b);
     float gr[KC][KC];  // upper: re at [k][l] (k <= l), im at [l][k] (l > k)
 #pragma unroll
@@ -83,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
       const int zz = (a.sz + j * b + cc) % nz;
       float2 xv[KC];
 #pragma unroll
-      for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[((m * K + k) * rb + r) * nz + zz] : make_float2(0.f, 0.f);
+      for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[(k * rb + r) * nz + zz] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < KC; ++k)
 #pragma unroll
@@ -106,30 +119,33 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
         for (int l = 0; l < KC; ++l) gram[blk * KC * KC + k * KC + l] = gr[k][l];
     }
   }
-  __syncthreads();
+}
 
-  // 3. eigendecomposition and threshold weights, one thread per block
-  for (int blk = threadIdx.x; blk < nblk; blk += kThreads)
-    svt_weights<ET, KC>(gram + blk * KC * KC, a.tau, wm + (size_t)blk * KC * KC);
-  __syncthreads();
+// 3. threshold weights, one thread per block, threads t0 .. t0 + nth - 1
+template <int KC, typename ET>
+__device__ __forceinline__ void llr_eigen(const float* gram, float tau, float2* wm, int nblk, int t0, int nth) {
+  for (int blk = (int)threadIdx.x - t0; blk < nblk; blk += nth)
+    svt_weights<ET, KC>(gram + blk * KC * KC, tau, wm + (size_t)blk * KC * KC);
+}
 
-  // 4. X' = X W, then FISTA momentum; write back.  The optional convergence monitor sums
-  // |x_{k+1} - x_k|^2 and |x_{k+1}|^2 in float32 per thread (float64 only for the
-  // cross-thread reduction: the float64 pipe is a small fraction of float32 on GB300).
-  const bool want_res = (FISTA || MODE == LLR_ADMM) && a.res != nullptr;
-  float d2 = 0.f, x2 = 0.f;
-  const int npx = M * rb * nz;
-  for (int e = threadIdx.x; e < npx; e += kThreads) {
+// 4. X' = X W, then the FISTA momentum or the ADMM dual; write back.  The optional
+// convergence monitor sums |change|^2 and |new|^2 in float32 per thread.
+template <int KC, int MODE>
+__device__ __forceinline__ void llr_apply(const Geom& g, const FistaArgs& a, const LlrUnit& un, const float2* gs,
+                                          const float2* wm, float2* x, float2* z, float2* u, bool want_res, float& d2,
+                                          float& x2) {
+  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, b = a.b, rb = un.rb;
+  const int npx = rb * nz;
+  for (int e = threadIdx.x; e < npx; e += blockDim.x) {
     const int zz = e % nz;
-    const int rest = e / nz;
-    const int r = rest % rb, m = rest / rb;
-    const int y = (a.sy + band * b + r) % ny;
+    const int r = e / nz;
+    const int y = (a.sy + un.band * b + r) % ny;
     const int j = (((zz - a.sz) % nz + nz) % nz) / b;
-    const float2* w = wm + (size_t)(m * nbz + j) * KC * KC;
+    const float2* w = wm + (size_t)j * KC * KC;
     float2 xv[KC];
 #pragma unroll
-    for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[((m * K + k) * rb + r) * nz + zz] : make_float2(0.f, 0.f);
-    const long long gb = ((long long)(s * MS + m0 + m) * K) * N + (long long)y * nz + zz;
+    for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[(k * rb + r) * nz + zz] : make_float2(0.f, 0.f);
+    const long long gb = ((long long)(un.s * g.M + un.m0) * K) * N + (long long)y * nz + zz;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       if (k < K) {
@@ -147,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
           u[gi] = csub(xv[k], o);
           continue;
         }
-        if (FISTA) {
+        if (MODE == LLR_FISTA) {
           const float2 xo = x[gi];
           const float2 dx = csub(o, xo);
           z[gi] = make_float2(o.x + a.beta * dx.x, o.y + a.beta * dx.y);
@@ -160,27 +176,61 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
       }
     }
   }
-  if (want_res) {
-    double dd = d2, xx = x2;
+}
+
+// float32 per-thread sums of the monitor, float64 across threads (the float64 pipe is a
+// small fraction of float32 on GB300)
+__device__ __forceinline__ void llr_res_flush(double* res, float d2, float x2) {
+  double dd = d2, xx = x2;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      dd += __shfl_xor_sync(0xffffffffu, dd, o);
-      xx += __shfl_xor_sync(0xffffffffu, xx, o);
-    }
-    if (lane == 0) {
-      atomicAdd(a.res, dd);
-      atomicAdd(a.res + 1, xx);
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    xx += __shfl_xor_sync(0xffffffffu, xx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(res, dd);
+    atomicAdd(res + 1, xx);
   }
 }
 
+template <int KC>
+__host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
+  return sizeof(float2) * ((size_t)K * b * nz + (size_t)((nz + b - 1) / b) * KC * KC) +
+         sizeof(float) * (size_t)((nz + b - 1) / b) * KC * KC;
+}
+
+// The K <= 4 float32 variant is held to 80 registers so that three CTAs share an SM and
+// the single-thread eigen-steps of one band overlap the memory phases of the others.
+// MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
+// z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
+// u <- w - v.
 template <int KC, int MODE, typename ET>
-static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
-                          const float2* aty, float2* u, cudaStream_t st) {
+__global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1)
+    k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
+          const float2* __restrict__ aty, float2* u) {
+  extern __shared__ float2 smem[];
+  const int nbands = (g.ny + a.b - 1) / a.b;
+  const LlrUnit un = llr_unit(g, a.b, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x);
   const int nbz = (g.nz + a.b - 1) / a.b;
-  const int nblk = nbz;  // per map set
-  const size_t sm = sizeof(float2) * ((size_t)g.K * a.b * g.nz + (size_t)nblk * KC * KC) +
-                    sizeof(float) * (size_t)nblk * KC * KC;
+  float2* gs = smem;                                         // [K][rb][nz]
+  float2* wm = gs + (size_t)g.K * un.rb * g.nz;              // [nbz][KC][KC]
+  float* gram = reinterpret_cast<float*>(wm + (size_t)nbz * KC * KC);  // [nbz][KC*KC]
+  llr_gather<MODE>(g, a, un, gs, x, z, grad, aty, u, 0, kThreads);
+  __syncthreads();
+  llr_gram<KC>(g, a, un, gs, gram, 0, kThreads / 32);
+  __syncthreads();
+  llr_eigen<KC, ET>(gram, a.tau, wm, nbz, 0, kThreads);
+  __syncthreads();
+  const bool want_res = (MODE == LLR_FISTA || MODE == LLR_ADMM) && a.res != nullptr;
+  float d2 = 0.f, x2 = 0.f;
+  llr_apply<KC, MODE>(g, a, un, gs, wm, x, z, u, want_res, d2, x2);
+  if (want_res) llr_res_flush(a.res, d2, x2);
+}
+
+template <int KC, int MODE, typename ET>
+cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad, const float2* aty,
+                   float2* u, cudaStream_t st) {
+  const size_t sm = llr_unit_bytes<KC>(g.K, a.b, g.nz);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_llr<KC, MODE, ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -193,14 +243,16 @@ static cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* 
 }
 
 template <int MODE>
-static cudaError_t llr_mode(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
-                            const float2* aty, float2* u, cudaStream_t st) {
+cudaError_t llr_mode(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad, const float2* aty,
+                     float2* u, cudaStream_t st) {
   if (a.eig64)
     return g.K <= 4 ? llr_go<4, MODE, double>(g, a, x, z, grad, aty, u, st)
                     : llr_go<8, MODE, double>(g, a, x, z, grad, aty, u, st);
   return g.K <= 4 ? llr_go<4, MODE, float>(g, a, x, z, grad, aty, u, st)
                   : llr_go<8, MODE, float>(g, a, x, z, grad, aty, u, st);
 }
+
+}  // namespace
 
 cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                        const float2* aty, cudaStream_t st) {
@@ -214,9 +266,7 @@ cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alp
 }
 
 size_t llr_smem_bytes(const Geom& g, int b) {
-  const int kc = g.K <= 4 ? 4 : 8;
-  const int nblk = (g.nz + b - 1) / b;  // one map set per CTA
-  return sizeof(float2) * ((size_t)g.K * b * g.nz + (size_t)nblk * kc * kc) + sizeof(float) * (size_t)nblk * kc * kc;
+  return g.K <= 4 ? llr_unit_bytes<4>(g.K, b, g.nz) : llr_unit_bytes<8>(g.K, b, g.nz);
 }
 
 }  // namespace t2sh
