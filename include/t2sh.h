@@ -306,6 +306,15 @@ t2sh_status t2sh_configure(t2sh_plan_t plan, int32_t col_variant, int32_t fused_
  */
 t2sh_status t2sh_sync(t2sh_plan_t plan);
 
+/*
+ * t2sh_wait_selftest -- exercises the bounded-wait failure path without a fault: a kernel
+ * on the plan's stream waits, through the same bounded wait the tile kernels use, on a
+ * barrier that nothing completes, gives up after limit_ns (1 .. 1e9 ns) and records the
+ * timeout; the next t2sh_sync returns T2SH_ETIMEOUT and clears it, and the plan stays
+ * usable.  The paper has no counterpart.
+ */
+t2sh_status t2sh_wait_selftest(t2sh_plan_t plan, uint64_t limit_ns);
+
 /* The step mu the plan uses (host float). */
 t2sh_status t2sh_get_step(t2sh_plan_t plan, float* step);
 

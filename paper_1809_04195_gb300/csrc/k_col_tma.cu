@@ -191,6 +191,24 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
   }
 }
 
+// Self-test of the bounded-wait path: one thread waits on an mbarrier that nothing
+// completes, with a limit of limit_ns, and records the timeout in the error flag exactly
+// as the tile kernels do.  Nothing is in flight, so the kernel simply returns.
+__global__ void k_wait_selftest(int* err, unsigned long long limit_ns) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_ns) && err) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_selftest(int* err, unsigned long long limit_ns, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
 TmaEncodeFn tma_encode_fn() {
   static TmaEncodeFn fn = nullptr;

@@ -483,9 +483,16 @@ t2sh_status t2sh_sync(t2sh_plan_t p) {
   T2SH_CK(cudaMemcpy(&flag, p->g.err, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     T2SH_CK(cudaMemset(p->g.err, 0, sizeof(int)));
-    set_err("a bounded device wait ran out (a tile copy did not complete in time)");
+    set_err("a bounded device wait ran out (a copy or tensor-core operation did not complete in time)");
     return T2SH_ETIMEOUT;
   }
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_wait_selftest(t2sh_plan_t p, uint64_t limit_ns) {
+  T2SH_REQ(p, "NULL plan");
+  T2SH_REQ(limit_ns >= 1 && limit_ns <= 1000000000ull, "limit_ns must be in [1, 1e9]");
+  T2SH_CK(launch_wait_selftest(p->g.err, (unsigned long long)limit_ns, p->st));
   return T2SH_OK;
 }
 

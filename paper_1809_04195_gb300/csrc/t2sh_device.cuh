@@ -585,12 +585,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// wait for phase `phase` of the barrier; false if it has not completed within kWaitNs
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
+// wait for phase `phase` of the barrier; false if it has not completed within limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase,
+                                                  unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, phase)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, phase))
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 

@@ -126,6 +126,7 @@ using TmaEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 TmaEncodeFn tma_encode_fn();
+cudaError_t launch_wait_selftest(int* err, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_col_normal_pr(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 cudaError_t launch_col_normal_tc(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 cudaError_t launch_col_normal_tma(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);

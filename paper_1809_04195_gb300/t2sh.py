@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
             "t2sh_autotune": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
             "t2sh_sync": [_vp],
             "t2sh_configure": [_vp, _i32, _i32],
+            "t2sh_wait_selftest": [_vp, _u64],
             "t2sh_timing_read": [_vp, _i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
@@ -390,6 +391,11 @@ class Plan:
         """Pin the column-pass variant (0 TMA x8, 4 TMA x4, 1 cp.async x8, 2 cp.async x4,
         3 tensor cores in split BF16) and row fusion."""
         _check(lib().t2sh_configure(self._h, int(col_variant), 1 if fused_rows else 0))
+
+    def wait_selftest(self, limit_ns: int):
+        """Launch a kernel whose bounded wait runs out after limit_ns; the next sync()
+        raises T2shError(ETIMEOUT) and the plan stays usable."""
+        _check(lib().t2sh_wait_selftest(self._h, int(limit_ns)))
 
     def sync(self):
         """Synchronise the plan's stream; raises T2shError(ETIMEOUT) if a bounded device
