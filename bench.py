@@ -44,6 +44,8 @@ def parse():
                     help="mixed: column DFTs as split-BF16 GEMMs on the tensor cores (FP32 accumulation)")
     ap.add_argument("--form", choices=["batched", "per-slice"], default="batched",
                     help="per-slice: one plan and one solve per slice (the plain per-slice form)")
+    ap.add_argument("--col-variant", type=int, default=None,
+                    help="pin the column-pass variant (t2sh_configure); default: the plan's own choice")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solver", choices=["fista", "admm"], default="fista",
@@ -278,6 +280,8 @@ def run_ours(args):
                 p.close()
             return {k: tuple(v) for k, v in tm.items()} if timing else None
         p = t2sh.Plan(dims, phi_d, mask_d, maps_d)
+        if args.col_variant is not None:
+            p.configure(args.col_variant)
         if timing:
             p.timing(True)
         if args.solver == "admm":
@@ -396,7 +400,8 @@ def run_ours(args):
             "data": "synthetic (seeded 3D ellipsoid knee phantom, smooth coil maps, variable-density masks)",
             "config": {**config_dict(sh, S, iters, world), "precision": args.precision, "form": args.form,
                        **({"solver": f"admm rho={args.rho} cg_iters={args.cg_iters}"} if args.solver == "admm" else {}),
-                       **({"post_te": post_te} if post_te else {})}, "roofline": roof, "gpu_launches": launches,
+                       **({"post_te": post_te} if post_te else {}),
+                       **({"col_variant": args.col_variant} if args.col_variant is not None else {})}, "roofline": roof, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": e2e}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sh)

@@ -119,8 +119,15 @@ typedef struct t2sh_plan_s* t2sh_plan_t;
 t2sh_status t2sh_plan(const t2sh_dims* dims, const float* phi, const uint8_t* mask,
                       const void* maps, void* stream, t2sh_plan_t* out);
 
-/* Release every device buffer of the plan (after synchronising its stream). */
+/* Release every device buffer of the plan (after synchronising its stream).  Plan
+ * buffers come from a library-owned, stream-ordered memory pool of the current device
+ * that keeps released memory for the next plan (no fresh page mapping per plan); the
+ * pool's unused memory goes back to the device with t2sh_release_cached. */
 t2sh_status t2sh_destroy(t2sh_plan_t plan);
+
+/* t2sh_release_cached -- return the pool's unused memory on the current device to the
+ * device (memory of live plans stays).  Errors: ECUDA. */
+t2sh_status t2sh_release_cached(void);
 
 /*
  * t2sh_forward -- y = A x = P F S Phi x (Eq. 5 forward model; Eq. 1 per echo).

@@ -52,8 +52,9 @@ void set_err(const char* fmt, ...) {
     }                              \
   } while (0)
 
-// Stream-ordered pool for the host-IO k-space stage, one per device, keeping its memory
-// (release threshold at the maximum) so that plans made one after another reuse it.
+// Stream-ordered pool for every plan buffer and the host-IO k-space stage, one per device,
+// keeping its memory (release threshold at the maximum) so that plans made one after
+// another reuse it instead of mapping fresh pages; t2sh_release_cached returns it.
 cudaMemPool_t stage_pool() {
   static std::mutex mu;
   static std::map<int, cudaMemPool_t> pools;
@@ -199,7 +200,7 @@ struct t2sh_plan_s {
   size_t stage_bytes = 0;
   std::vector<int32_t> shifts;
   float mu = 1.f;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, bool>> allocs;  // (pointer, from the stage pool)
   // resumable FISTA state (t2sh_solve_begin / _iterate / _end)
   bool begun = false;
   int iter_done = 0;
@@ -220,23 +221,45 @@ struct t2sh_plan_s {
   float2* cg_p = nullptr;
   double* cg_red = nullptr;
 
+  // Plan buffers come from the stage pool in the plan stream's order (plain cudaMalloc if
+  // the pool is unavailable).  A pool allocation that fails is retried once after the
+  // pool's unused memory has been returned.
   template <typename T>
   t2sh_status alloc(T** p, size_t bytes) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    const size_t b = bytes ? bytes : 16;
+    cudaMemPool_t pool = stage_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, b, pool, st) : cudaMalloc(&q, b);
+    if (e != cudaSuccess && pool) {
+      cudaGetLastError();
+      cudaStreamSynchronize(st);
+      cudaMemPoolTrimTo(pool, 0);
+      e = cudaMallocFromPoolAsync(&q, b, pool, st);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
-      set_err("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+      set_err("allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
       return T2SH_ENOMEM;
     }
-    allocs.push_back(q);
+    allocs.emplace_back(q, pool != nullptr);
     *p = static_cast<T*>(q);
     return T2SH_OK;
   }
   ~t2sh_plan_s() {
+    if (cs) cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(st);
     for (cudaEvent_t e : cev) cudaEventDestroy(e);
     if (cs) cudaStreamDestroy(cs);
-    for (void* p : allocs) cudaFree(p);
+    bool pooled = false;
+    for (auto& a : allocs) {
+      if (a.second) {
+        cudaFreeAsync(a.first, st);
+        pooled = true;
+      } else {
+        cudaFree(a.first);
+      }
+    }
+    if (pooled) cudaStreamSynchronize(st);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
   cudaEvent_t next_event() {
@@ -436,6 +459,13 @@ t2sh_status t2sh_destroy(t2sh_plan_t p) {
     cudaStreamSynchronize(p->st);
   }
   delete p;
+  return T2SH_OK;
+}
+
+t2sh_status t2sh_release_cached(void) {
+  cudaMemPool_t pool = stage_pool();
+  if (!pool) return T2SH_OK;
+  T2SH_CK(cudaMemPoolTrimTo(pool, 0));
   return T2SH_OK;
 }
 

@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
         sig = {
             "t2sh_plan": [ctypes.POINTER(Dims), _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)],
             "t2sh_destroy": [_vp],
+            "t2sh_release_cached": [],
             "t2sh_forward": [_vp, _vp, _vp, _i32],
             "t2sh_adjoint": [_vp, _vp, _i32, _vp],
             "t2sh_normal_op": [_vp, _vp, _vp],
@@ -122,6 +123,11 @@ def shifts(seed: int, iters: int, block: int) -> np.ndarray:
     out = np.zeros((max(iters, 0), 2), np.int32)
     _check(lib().t2sh_shifts(seed, iters, block, out.ctypes.data_as(ctypes.POINTER(_i32))))
     return out
+
+
+def release_cached() -> None:
+    """Return the unused memory of the library's plan pool to the device."""
+    _check(lib().t2sh_release_cached())
 
 
 def workspace_bytes(dims: Dims) -> int:

@@ -61,3 +61,35 @@ def test_bounded_wait_timeout_is_reported_and_the_plan_stays_usable(T):
             p2.wait_selftest(0)
         finally:
             p2.close()
+
+
+def test_plan_memory_is_reused_bitwise_and_released(T):
+    """Plan buffers come from the library's stream-ordered pool.  A second plan made after
+    the first is destroyed reuses that memory (free device memory does not drop again),
+    solves bitwise like the first although its buffers still hold the first plan's data,
+    and release_cached hands the cached memory back to the device."""
+    S, ny, nz, C, Tn, K = 48, 128, 96, 8, 16, 4
+    rng, phi, mask, maps = random_problem(53, S, ny, nz, C, Tn, K, 1)
+    y = c64(crandn(rng, S, C, Tn, ny, nz) * mask[None, None] * 0.1)
+    d = T.make_dims(ny, nz, C, Tn, K, nslices=S, block=8, lam=0.02, iters=4, seed=3)
+    ws = T.workspace_bytes(d)
+    assert ws > 200e6
+    torch.cuda.synchronize()
+    T.release_cached()
+    free0 = torch.cuda.mem_get_info()[0]
+    torch0 = torch.cuda.memory_reserved()
+    outs, live = [], []
+    for _ in range(2):
+        with make_plan(T, phi, mask, maps, block=8, lam=0.02, iters=4, seed=3) as p:
+            outs.append(host(p.solve(y, T.KSPACE_TE)))
+            p.sync()
+            live.append(torch.cuda.mem_get_info()[0])
+    cached = torch.cuda.mem_get_info()[0]
+    assert np.array_equal(outs[0], outs[1])
+    assert free0 - live[0] > 0.9 * ws
+    assert abs(live[1] - live[0]) < 0.1 * ws  # the second plan took no new memory
+    assert free0 - cached > 0.9 * ws          # destroyed plans' memory stays cached
+    T.release_cached()
+    # what torch's own allocator kept of the solve outputs is not the plan pool's
+    torch_kept = torch.cuda.memory_reserved() - torch0
+    assert free0 - torch.cuda.mem_get_info()[0] - torch_kept < 0.1 * ws
