@@ -23,9 +23,11 @@ using Ex = ExLayout<R1>;
 
 // ------------------------------------------------------------------------------------
 // Row pass.  CTA = (slice, band of RB rows), 16 x 4 x RB threads, thread
-// (j, line = k * RB + r).  K <= 4, M <= 2.  RB = 8 for the forward pass; 4 for the
-// adjoint pass (its double-buffered t rows) and wherever 8 would not fit in shared
-// memory (N >= 240 or two map sets).
+// (j, line = k * RB + r).  K <= 4, M <= 2.  With one map set and N < 240 the bands are
+// two rows (128 threads) and the kernel is held to 64 registers (forward, eight CTAs per
+// SM) or 80 (adjoint, six): many small CTAs keep the SM issuing while others wait at
+// their per-coil barriers (forward 1.47 -> 1.18 ms on the knee scan against bands of 8
+// rows).  N >= 240 and two map sets keep bands of 4 rows without a block bound.
 // ------------------------------------------------------------------------------------
 // Padded strides (float2) of the row pass's exchange lines (LX) and staged map rows (MS).
 // The packed second stage reads R1 consecutive items from each of several lines per
@@ -43,13 +45,15 @@ struct RowPad {
 
 template <int N, int MC, int MODE>
 struct RowFastRB {
-  static constexpr int value = (N >= 240 || MC == 2 || MODE == ROW_ADJ) ? 4 : 8;
+  static constexpr bool small = MC == 1 && N < 240;  // two-row bands, occupancy-bounded kernel
+  static constexpr int value = small ? 2 : 4;
+  static constexpr int min_blocks = MODE == ROW_FWD ? 8 : 6;
 };
 
 template <int N, int MODE, int MC, int kRowRB = RowFastRB<N, MC, MODE>::value>
-__global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* __restrict__ tw_g,
-                                                 const float2* __restrict__ maps, const float2* __restrict__ x,
-                                                 float2* __restrict__ t, float2* __restrict__ out) {
+__device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __restrict__ tw_g,
+                                              const float2* __restrict__ maps, const float2* __restrict__ x,
+                                              float2* __restrict__ t, float2* __restrict__ out) {
   constexpr int R1 = N / 16;
   constexpr int LINE = RowPad<N>::LX;
   // the adjoint keeps unpadded map rows: at N = 160 the padding would cost it its third
@@ -181,6 +185,20 @@ __global__ void __launch_bounds__(64 * kRowRB) k_row_fast(Geom g, const float2* 
         for (int q = 0; q < 16; ++q) op[R1 * q] = acc[m][q];
       }
   }
+}
+
+template <int N, int MODE, int MC>
+__global__ void __launch_bounds__(64 * RowFastRB<N, MC, MODE>::value, RowFastRB<N, MC, MODE>::min_blocks)
+    k_row_fast(Geom g, const float2* __restrict__ tw_g, const float2* __restrict__ maps,
+               const float2* __restrict__ x, float2* __restrict__ t, float2* __restrict__ out) {
+  row_fast_body<N, MODE, MC>(g, tw_g, maps, x, t, out);
+}
+
+template <int N, int MODE, int MC>
+__global__ void __launch_bounds__(64 * RowFastRB<N, MC, MODE>::value)
+    k_row_fast_wide(Geom g, const float2* __restrict__ tw_g, const float2* __restrict__ maps,
+                    const float2* __restrict__ x, float2* __restrict__ t, float2* __restrict__ out) {
+  row_fast_body<N, MODE, MC>(g, tw_g, maps, x, t, out);
 }
 
 // ------------------------------------------------------------------------------------
@@ -356,17 +374,21 @@ static size_t row_fast_smem() {
 template <int N, int MODE, int MC>
 static cudaError_t row_fast_go(const Geom& g, const float2* tw, const float2* maps, const float2* x, float2* t,
                                float2* out, cudaStream_t st) {
-  constexpr int RB = RowFastRB<N, MC, MODE>::value;
+  using RF = RowFastRB<N, MC, MODE>;
+  constexpr int RB = RF::value;
   const size_t sm = row_fast_smem<N, MODE, MC>();
+  auto kern = [] {
+    if constexpr (RF::small) return k_row_fast<N, MODE, MC>;
+    else return k_row_fast_wide<N, MODE, MC>;
+  }();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_row_fast<N, MODE, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((g.ny + RB - 1) / RB, g.S);
-  k_row_fast<N, MODE, MC><<<grid, 64 * RB, sm, st>>>(g, tw, maps, x, t, out);
+  kern<<<grid, 64 * RB, sm, st>>>(g, tw, maps, x, t, out);
   return cudaGetLastError();
 }
 

@@ -199,13 +199,15 @@ __host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
          sizeof(float) * (size_t)((nz + b - 1) / b) * KC * KC;
 }
 
-// The K <= 4 float32 variant is held to 80 registers so that three CTAs share an SM and
-// the single-thread eigen-steps of one band overlap the memory phases of the others.
+// The K <= 4 float32 variant is held to 80 registers (three CTAs per SM) or, where four
+// CTAs' shared memory fits on an SM, to 64 registers (four per SM; a few values spill to
+// L1), so that the single-thread eigen-steps of one band overlap the memory phases of the
+// others: 0.735 -> 0.649 ms on the knee scan with four.
 // MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
 // z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
 // u <- w - v.
-template <int KC, int MODE, typename ET>
-__global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1)
+template <int KC, int MODE, typename ET, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
           const float2* __restrict__ aty, float2* u) {
   extern __shared__ float2 smem[];
@@ -227,19 +229,32 @@ __global__ void __launch_bounds__(kThreads, (KC == 4 && sizeof(ET) == 4) ? 3 : 1
   if (want_res) llr_res_flush(a.res, d2, x2);
 }
 
-template <int KC, int MODE, typename ET>
-cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad, const float2* aty,
-                   float2* u, cudaStream_t st) {
-  const size_t sm = llr_unit_bytes<KC>(g.K, a.b, g.nz);
+template <int KC, int MODE, typename ET, int MINB>
+cudaError_t llr_launch(const Geom& g, const FistaArgs& a, size_t sm, float2* x, float2* z, const float2* grad,
+                       const float2* aty, float2* u, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_llr<KC, MODE, ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_llr<KC, MODE, ET, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((g.ny + a.b - 1) / a.b, g.S, g.M);
-  k_llr<KC, MODE, ET><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty, u);
+  k_llr<KC, MODE, ET, MINB><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty, u);
   return cudaGetLastError();
+}
+
+template <int KC, int MODE, typename ET>
+cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad, const float2* aty,
+                   float2* u, cudaStream_t st) {
+  const size_t sm = llr_unit_bytes<KC>(g.K, a.b, g.nz);
+  if constexpr (KC == 4 && sizeof(ET) == 4) {
+    // four CTAs per SM where their shared memory (plus the 1 KB each reserves) fits in 228 KB
+    if (4 * (sm + 1024) <= 228 * 1024) return llr_launch<KC, MODE, ET, 4>(g, a, sm, x, z, grad, aty, u, st);
+    return llr_launch<KC, MODE, ET, 3>(g, a, sm, x, z, grad, aty, u, st);
+  } else {
+    return llr_launch<KC, MODE, ET, 1>(g, a, sm, x, z, grad, aty, u, st);
+  }
 }
 
 template <int MODE>
