@@ -76,24 +76,25 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
   float2* tst = mst + 2 * MC * kRowRB * MS;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
 
+  // 16-byte copies of the coil's map rows (and, for the adjoint, its t rows) walked over
+  // (plane, row < RB, column pair) with compile-time divisors; rows past a partial band's
+  // end are skipped
   auto issue = [&](int c, int buf) {
+    constexpr int H = N / 2;  // 16-byte copies per row
     const float2* mp = maps + ((long long)(s * g.C + c) * M) * NN + (long long)y0 * N;
     float2* md = mst + buf * MC * kRowRB * MS;
-    const int nm = M * rb * N / 2;
-    for (int e2 = threadIdx.x; e2 < nm; e2 += blockDim.x) {
-      const int e = 2 * e2;
-      const int m = e / (rb * N), rem = e - m * rb * N;
-      const int row = rem / N, col = rem - row * N;
-      cp_async16(md + (m * kRowRB + row) * MS + col, mp + (long long)m * NN + rem);
+    for (int e2 = threadIdx.x; e2 < M * kRowRB * H; e2 += blockDim.x) {
+      const int line = e2 / H, col = 2 * (e2 - line * H);
+      const int m = line / kRowRB, row = line - m * kRowRB;
+      if (row < rb) cp_async16(md + line * MS + col, mp + (long long)m * NN + row * N + col);
     }
     if (MODE == ROW_ADJ) {
       const float2* tp = t + ((long long)(s * g.C + c) * K) * NN + (long long)y0 * N;
       float2* td = tst + buf * NL * N;
-      const int nt = K * rb * N / 2;
-      for (int e2 = threadIdx.x; e2 < nt; e2 += blockDim.x) {
-        const int e = 2 * e2;
-        const int kk = e / (rb * N), rem = e - kk * rb * N;
-        cp_async16(td + (kk * kRowRB) * N + rem, tp + (long long)kk * NN + rem);
+      for (int e2 = threadIdx.x; e2 < K * kRowRB * H; e2 += blockDim.x) {
+        const int line = e2 / H, col = 2 * (e2 - line * H);
+        const int kk = line / kRowRB, row = line - kk * kRowRB;
+        if (row < rb) cp_async16(td + line * N + col, tp + (long long)kk * NN + row * N + col);
       }
     }
   };

@@ -40,23 +40,50 @@ __device__ __forceinline__ LlrUnit llr_unit(const Geom& g, int b, int unit) {
   return un;
 }
 
-// 1. gather the band into gs [K][rb][nz] (gradient step fused for FISTA), two pixels per
-// float4, threads t0 .. t0 + nth - 1 of the CTA
+// Rows of the band as stored in gs are walked by P = nth / H groups of H = nz / 2 threads,
+// one pixel pair (a float4) per thread and row, so that the column-dependent quantities
+// of a thread are formed once and a row step is an add and a conditional subtract
+// (nz <= 512 keeps H <= 256 and P >= 1).  y of band row r is the shifted image row.
+struct LlrCols {
+  int tid, H, P, lp, c2;  // thread in the phase, pixel pairs per row, rows per pass, first row, pair
+  bool active;
+};
+__device__ __forceinline__ LlrCols llr_cols(int nz, int t0, int nth) {
+  LlrCols c;
+  c.tid = (int)threadIdx.x - t0;
+  c.H = nz >> 1;
+  c.P = nth / c.H;
+  c.lp = c.tid / c.H;
+  c.c2 = c.tid - c.lp * c.H;
+  c.active = c.tid >= 0 && c.lp < c.P;
+  return c;
+}
+__device__ __forceinline__ int llr_row0(const Geom& g, const FistaArgs& a, const LlrUnit& un) {
+  const int y = a.sy % g.ny + un.band * a.b;  // a shift may exceed a small image: reduce it first
+  return y >= g.ny ? y - g.ny : y;
+}
+
+// 1. gather the band into gs [K][rb][nz] (gradient step fused for FISTA), threads
+// t0 .. t0 + nth - 1 of the CTA
 template <int MODE>
 __device__ __forceinline__ void llr_gather(const Geom& g, const FistaArgs& a, const LlrUnit& un, float2* gs,
                                            const float2* x, const float2* z, const float2* __restrict__ grad,
                                            const float2* __restrict__ aty, const float2* u, int t0, int nth) {
-  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, b = a.b, rb = un.rb;
-  const int nel2 = (K * rb * nz) >> 1;
+  const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, rb = un.rb;
+  const LlrCols c = llr_cols(nz, t0, nth);
+  if (!c.active) return;
+  const int y0 = llr_row0(g, a, un);
+  const long long base = ((long long)un.s * g.M + un.m0) * K * (long long)N + 2 * c.c2;
+  int k = 0, r = c.lp;
+  while (r >= rb) {
+    r -= rb;
+    ++k;
+  }
 #pragma unroll 4
-  for (int e2 = (int)threadIdx.x - t0; e2 < nel2; e2 += nth) {
-    const int e = 2 * e2;
-    const int zz = e % nz;
-    int rest = e / nz;
-    const int r = rest % rb;
-    rest /= rb;  // k
-    const int y = (a.sy + un.band * b + r) % ny;
-    const long long gi = (((long long)un.s * g.M + un.m0) * K + rest) * N + (long long)y * nz + zz;
+  for (int l = c.lp; l < K * rb; l += c.P) {
+    int y = y0 + r;
+    y -= y >= ny ? ny : 0;
+    const long long gi = base + (long long)k * N + (long long)y * nz;
     float4 v;
     if (MODE == LLR_ADMM) {
       const float4 av = *reinterpret_cast<const float4*>(x + gi);
@@ -71,8 +98,12 @@ __device__ __forceinline__ void llr_gather(const Geom& g, const FistaArgs& a, co
     } else {
       v = *reinterpret_cast<const float4*>(x + gi);
     }
-    gs[e] = make_float2(v.x, v.y);
-    gs[e + 1] = make_float2(v.z, v.w);
+    *reinterpret_cast<float4*>(gs + (long long)l * nz + 2 * c.c2) = v;
+    r += c.P;
+    while (r >= rb) {
+      r -= rb;
+      ++k;
+    }
   }
 }
 
@@ -91,9 +122,11 @@ __device__ __forceinline__ void llr_gram(const Geom& g, const FistaArgs& a, cons
     for (int k = 0; k < KC; ++k)
 #pragma unroll
       for (int l = 0; l < KC; ++l) gr[k][l] = 0.f;
-    for (int p = lane; p < rb * cb; p += 32) {
-      const int r = p / cb, cc = p - r * cb;
-      const int zz = (a.sz + j * b + cc) % nz;
+    // lane (r0, cc) takes column cc of rows r0, r0 + RP, ... of the block
+    const int RP = 32 / cb, r0 = lane / cb, cc = lane - r0 * cb;
+    int zz = a.sz % nz + j * b + cc;  // j b + cc < nz, so zz < 2 nz
+    zz -= zz >= nz ? nz : 0;
+    for (int r = r0 < RP ? r0 : rb; r < rb; r += RP) {
       float2 xv[KC];
 #pragma unroll
       for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[(k * rb + r) * nz + zz] : make_float2(0.f, 0.f);
@@ -135,44 +168,60 @@ __device__ __forceinline__ void llr_apply(const Geom& g, const FistaArgs& a, con
                                           const float2* wm, float2* x, float2* z, float2* u, bool want_res, float& d2,
                                           float& x2) {
   const int ny = g.ny, nz = g.nz, N = ny * nz, K = g.K, b = a.b, rb = un.rb;
-  const int npx = rb * nz;
-  for (int e = threadIdx.x; e < npx; e += blockDim.x) {
-    const int zz = e % nz;
-    const int r = e / nz;
-    const int y = (a.sy + un.band * b + r) % ny;
-    const int j = (((zz - a.sz) % nz + nz) % nz) / b;
-    const float2* w = wm + (size_t)j * KC * KC;
-    float2 xv[KC];
+  const LlrCols c = llr_cols(nz, 0, blockDim.x);
+  if (!c.active) return;
+  // the two pixels of this thread's pair and the blocks they fall in (the band's columns
+  // are shifted by sz: block j holds the columns (sz + j b + 0 .. b - 1) mod nz)
+  const int zz = 2 * c.c2;
+  int d0 = zz - a.sz % nz;
+  d0 += d0 < 0 ? nz : 0;
+  const int d1 = d0 + 1 == nz ? 0 : d0 + 1;
+  const float2* w0 = wm + (size_t)(d0 / b) * KC * KC;
+  const float2* w1 = wm + (size_t)(d1 / b) * KC * KC;
+  const int y0 = llr_row0(g, a, un);
+  const long long gb0 = ((long long)(un.s * g.M + un.m0) * K) * N + zz;
+  for (int r = c.lp; r < rb; r += c.P) {
+    int y = y0 + r;
+    y -= y >= ny ? ny : 0;
+    float4 xv[KC];  // (pixel zz, pixel zz + 1) of each basis image
 #pragma unroll
-    for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[(k * rb + r) * nz + zz] : make_float2(0.f, 0.f);
-    const long long gb = ((long long)(un.s * g.M + un.m0) * K) * N + (long long)y * nz + zz;
+    for (int k = 0; k < KC; ++k)
+      xv[k] = (k < K) ? *reinterpret_cast<const float4*>(gs + (k * rb + r) * nz + zz) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long gb = gb0 + (long long)y * nz;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       if (k < K) {
-        float2 o = make_float2(0.f, 0.f);
+        float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int l = 0; l < KC; ++l) cfma(o, xv[l], w[l * KC + k]);
+        for (int l = 0; l < KC; ++l) {
+          cfma(o0, make_float2(xv[l].x, xv[l].y), w0[l * KC + k]);
+          cfma(o1, make_float2(xv[l].z, xv[l].w), w1[l * KC + k]);
+        }
+        const float4 o = make_float4(o0.x, o0.y, o1.x, o1.y);
+        const float4 xk = xv[k];
         const long long gi = gb + (long long)k * N;
         if (MODE == LLR_ADMM) {
           if (want_res) {
-            const float2 dv = csub(o, z[gi]);
-            d2 = fmaf(dv.x, dv.x, fmaf(dv.y, dv.y, d2));
-            x2 = fmaf(o.x, o.x, fmaf(o.y, o.y, x2));
+            const float4 zo = *reinterpret_cast<const float4*>(z + gi);
+            const float dx0 = o.x - zo.x, dy0 = o.y - zo.y, dx1 = o.z - zo.z, dy1 = o.w - zo.w;
+            d2 = fmaf(dx0, dx0, fmaf(dy0, dy0, fmaf(dx1, dx1, fmaf(dy1, dy1, d2))));
+            x2 = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, x2))));
           }
-          z[gi] = o;
-          u[gi] = csub(xv[k], o);
+          *reinterpret_cast<float4*>(z + gi) = o;
+          *reinterpret_cast<float4*>(u + gi) = make_float4(xk.x - o.x, xk.y - o.y, xk.z - o.z, xk.w - o.w);
           continue;
         }
         if (MODE == LLR_FISTA) {
-          const float2 xo = x[gi];
-          const float2 dx = csub(o, xo);
-          z[gi] = make_float2(o.x + a.beta * dx.x, o.y + a.beta * dx.y);
+          const float4 xo = *reinterpret_cast<const float4*>(x + gi);
+          const float4 dx = make_float4(o.x - xo.x, o.y - xo.y, o.z - xo.z, o.w - xo.w);
+          *reinterpret_cast<float4*>(z + gi) =
+              make_float4(o.x + a.beta * dx.x, o.y + a.beta * dx.y, o.z + a.beta * dx.z, o.w + a.beta * dx.w);
           if (want_res) {
-            d2 = fmaf(dx.x, dx.x, fmaf(dx.y, dx.y, d2));
-            x2 = fmaf(o.x, o.x, fmaf(o.y, o.y, x2));
+            d2 = fmaf(dx.x, dx.x, fmaf(dx.y, dx.y, fmaf(dx.z, dx.z, fmaf(dx.w, dx.w, d2))));
+            x2 = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, x2))));
           }
         }
-        x[gi] = o;
+        *reinterpret_cast<float4*>(x + gi) = o;
       }
     }
   }
