@@ -230,6 +230,27 @@ def adjoint_data(kspace: np.ndarray, kform: str, maps: np.ndarray, mask: np.ndar
     raise ValueError(kform)
 
 
+def data_term(kspace: np.ndarray, kform: str, maps: np.ndarray, mask: np.ndarray, phi: np.ndarray,
+              alpha: np.ndarray) -> tuple[float, float]:
+    """Data term of Eq. 5 at alpha, f = 1/2 ||P F S Phi alpha - y||^2 over the acquired
+    samples, split as f = h + c with h = 1/2 <alpha, A^H A alpha> - Re <alpha, A^H y>
+    (the part that depends on alpha) and c = 1/2 ||P y||^2.
+
+    T-form data: f from its definition (the residual of the forward model), c from y,
+    h = f - c.  Projected data do not determine c (NaN); h is then formed from A^H A alpha
+    and A^H y (Sec. IV.B's normal operator and the projected adjoint)."""
+    if kform == "te":
+        y = mask[None].astype(float) * kspace
+        f = 0.5 * float(np.sum(np.abs(forward(alpha, maps, mask, phi) - y) ** 2))
+        c = 0.5 * float(np.sum(np.abs(y) ** 2))
+        return f - c, c
+    if kform == "proj":
+        w = normal(alpha, maps, space_time_kernel(mask, phi))
+        h = 0.5 * float(np.real(np.vdot(alpha, w))) - float(np.real(np.vdot(alpha, adjoint_projected(kspace, maps))))
+        return h, float("nan")
+    raise ValueError(kform)
+
+
 def fista(kspace: np.ndarray, kform: str, maps: np.ndarray, mask: np.ndarray, phi: np.ndarray,
           lam: float, b: int, iters: int, seed: int, step: float | None = None,
           shifts: bool = True, x0: np.ndarray | None = None, return_trace: bool = False):

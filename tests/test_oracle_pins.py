@@ -129,6 +129,30 @@ def test_forward_and_normal_match_dense_matrix(M):
     assert np.abs(nrm.ravel() - A.conj().T @ (A @ alpha.ravel())).max() < 1e-12
 
 
+@pytest.mark.parametrize("M", [1, 2])
+def test_data_term_matches_dense_least_squares(M):
+    """The data term of Eq. 5 against 1/2 ||A alpha - P y||^2 with the Kronecker-built A,
+    the split f = h + c, projected data (same h, c undetermined), f(alpha_true) = 0 on
+    noiseless data and h(0) = 0."""
+    phi, maps, mask, rng = tiny_problem(31 + M, M=M)
+    A = dense_A(maps, mask, phi)
+    alpha = crandn(rng, M, 2, 8, 8)
+    y = crandn(rng, 2, 6, 8, 8)
+    py = y * mask[None]
+    f_dense = 0.5 * np.sum(np.abs(A @ alpha.ravel() - py.ravel()) ** 2)
+    h, c = O.data_term(y, "te", maps, mask, phi, alpha)
+    assert abs(h + c - f_dense) < 1e-10 * f_dense
+    assert abs(c - 0.5 * np.sum(np.abs(py) ** 2)) < 1e-10 * c
+    # projected data: the same alpha-dependent part, from the expanded form
+    hp, cp = O.data_term(O.project(y, mask, phi), "proj", maps, mask, phi, alpha)
+    assert abs(hp - h) < 1e-10 * abs(h) and np.isnan(cp)
+    # noiseless data: the data term vanishes at the true coefficients
+    y0 = A @ alpha.ravel()
+    h0, c0 = O.data_term(y0.reshape(2, 6, 8, 8), "te", maps, mask, phi, alpha)
+    assert abs(h0 + c0) < 1e-10 * c0
+    assert O.data_term(y, "te", maps, mask, phi, np.zeros_like(alpha))[0] == 0.0
+
+
 def test_adjoint_identity_knee_like():
     rng = np.random.default_rng(5)
     T, K, C, M, ny, nz = 20, 4, 4, 2, 32, 24
