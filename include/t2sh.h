@@ -193,6 +193,24 @@ t2sh_status t2sh_solve_admm(t2sh_plan_t plan, const void* kspace, int32_t kform,
                             int32_t cg_iters, double* residual_out);
 
 /*
+ * t2sh_objective -- the data term of Eq. 5 at x for every slice,
+ *   f_s(x) = 1/2 || P F S Phi x_s - y_s ||^2 over the acquired samples,
+ * returned in two parts, f_s = h_s + c_s:
+ *   out[2 s]      h_s = 1/2 <x_s, A^H A x_s> - Re <x_s, A^H y_s>   (the part that depends on x)
+ *   out[2 s + 1]  c_s = 1/2 sum_{c,t,n} P_t(n) |y_{s,c,t}(n)|^2 for T-form k-space; NaN for
+ *                 projected k-space, which does not determine it.
+ *   kspace, kform  as for t2sh_solve (host pointers with T2SH_HOST_IO)
+ *   x              [S][M][K][ny][nz] complex (host with T2SH_HOST_IO)
+ *   out            host double[2 S]
+ * Inner products accumulate in float64 across threads.  One normal operator, one
+ * A^H y and the reductions; the plan's gradient and intermediate buffers are scratch,
+ * the solver state is not touched, so it may be called between t2sh_solve_iterate
+ * calls.  Synchronises the stream.  Errors: EINVAL, ENOMEM (first call allocates the
+ * accumulators), ECUDA.
+ */
+t2sh_status t2sh_objective(t2sh_plan_t plan, const void* kspace, int32_t kform, const void* x, double* out);
+
+/*
  * t2sh_postprocess -- TE images from reconstructed coefficients (the "Process TE" step of
  * Sec. III.C and the Reconstruction paragraph of Sec. V): for each requested echo
  * te_index[i] (rows of the plan's basis Phi, 0-based) and each slice,

@@ -8,6 +8,8 @@
 // float64 accumulator with one atomic.  The step a = <r,r> / <p,q> and the direction
 // weight b = <r_new,r_new> / <r,r> are formed on the device from those accumulators
 // (a zero denominator gives a zero quotient), so an iteration needs no host round trip.
+#include <algorithm>
+
 #include "t2sh_device.cuh"
 
 namespace t2sh {
@@ -179,6 +181,24 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_dir(long long L, const float2
 }
 #undef CG_INDEX
 
+// out[s] += sum_{c,t,n} P_t(n) |y_{s,c,t}(n)|^2 of T-form k-space y [S][C][T][N] (float64
+// per thread: a diagnostic reduction, not on the iteration path)
+__global__ void __launch_bounds__(kCgThreads) k_masked_energy(long long N, int C, int T, const uint8_t* __restrict__ mask,
+                                                             const float2* __restrict__ y, double* out) {
+  const int s = blockIdx.y;
+  const long long L = (long long)C * T * N;
+  const float2* ys = y + (long long)s * L;
+  double acc = 0.0;
+  for (long long n = (long long)blockIdx.x * kCgThreads + threadIdx.x; n < N; n += (long long)gridDim.x * kCgThreads)
+    for (int t = 0; t < T; ++t)
+      if (mask[(long long)t * N + n])
+        for (int c = 0; c < C; ++c) {
+          const float2 v = ys[((long long)c * T + t) * N + n];
+          acc += (double)v.x * v.x + (double)v.y * v.y;
+        }
+  block_add(acc, out + s);
+}
+
 dim3 cg_grid(const Geom& g, long long L) {
   const long long per_cta = 2LL * kCgThreads * kCgPerThread;
   return dim3((unsigned)((L + per_cta - 1) / per_cta), (unsigned)g.S);
@@ -204,6 +224,13 @@ cudaError_t launch_cg_step(const Geom& g, float2* x, float2* r, const float2* p,
                            const double* rr, const double* pq, double* rr_new, cudaStream_t st) {
   const long long L = (long long)g.M * g.K * g.ny * g.nz;
   k_cg_step<<<cg_grid(g, L), kCgThreads, 0, st>>>(L, x, r, p, w, rho, rr, pq, rr_new);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_masked_energy(const Geom& g, const uint8_t* mask, const float2* y, double* out, cudaStream_t st) {
+  const long long N = (long long)g.ny * g.nz;
+  const unsigned gx = (unsigned)std::min<long long>((N + kCgThreads - 1) / kCgThreads, 64);
+  k_masked_energy<<<dim3(gx, (unsigned)g.S), kCgThreads, 0, st>>>(N, g.C, g.T, mask, y, out);
   return cudaGetLastError();
 }
 

@@ -220,6 +220,10 @@ struct t2sh_plan_s {
   float2* cg_r = nullptr;
   float2* cg_p = nullptr;
   double* cg_red = nullptr;
+  // data-term diagnostic (t2sh_objective, allocated on its first call): per-slice float64
+  // accumulators [3][S] and, for host-buffer plans, a device copy of the evaluated x
+  double* obj = nullptr;
+  float2* ov = nullptr;
 
   // Plan buffers come from the stage pool in the plan stream's order (plain cudaMalloc if
   // the pool is unavailable).  A pool allocation that fails is retried once after the
@@ -980,6 +984,54 @@ done:
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   return st;
+}
+
+t2sh_status t2sh_objective(t2sh_plan_t p, const void* kspace, int32_t kform, const void* x, double* out) {
+  T2SH_REQ(p && kspace && x && out, "NULL argument");
+  T2SH_REQ(kform == T2SH_KSPACE_TE || kform == T2SH_KSPACE_PROJ, "bad kform %d", kform);
+  const t2sh_dims& d = p->d;
+  const int S = d.nslices;
+  const size_t vec = footprint(d).vec;
+  if (!p->obj) {
+    t2sh_status a = p->alloc(&p->obj, sizeof(double) * 3 * (size_t)S);
+    if (a != T2SH_OK) return a;
+  }
+  const void* ky = kspace;
+  const float2* xd = static_cast<const float2*>(x);
+  if (p->host_io) {
+    const size_t kb = kspace_bytes(d, kform);
+    t2sh_status se = ensure_stage(p, kb);
+    if (se != T2SH_OK) return se;
+    if (!p->ov) {
+      t2sh_status a = p->alloc(&p->ov, vec);
+      if (a != T2SH_OK) return a;
+    }
+    T2SH_CK(cudaMemcpyAsync(p->stage, kspace, kb, cudaMemcpyHostToDevice, p->st));
+    T2SH_CK(cudaMemcpyAsync(p->ov, x, vec, cudaMemcpyHostToDevice, p->st));
+    ky = p->stage;
+    xd = p->ov;
+  }
+  double* xx = p->obj;          // <x, A^H A x>
+  double* xa = p->obj + S;      // Re <x, A^H y>
+  double* yy = p->obj + 2 * S;  // ||P y||^2
+  T2SH_CK(cudaMemsetAsync(p->obj, 0, sizeof(double) * 3 * (size_t)S, p->st));
+  // the gradient buffer is scratch between iterations: A^H A x, then A^H y
+  t2sh_status s = normal_op(p, xd, p->grad);
+  if (s != T2SH_OK) return s;
+  T2SH_CK(launch_cg_dot(p->g, xd, p->grad, 0.f, xx, p->st));
+  s = adjoint_data(p, ky, kform, p->grad);
+  if (s != T2SH_OK) return s;
+  T2SH_CK(launch_cg_dot(p->g, xd, p->grad, 0.f, xa, p->st));
+  if (kform == T2SH_KSPACE_TE)
+    T2SH_CK(launch_masked_energy(p->g, p->mask, static_cast<const float2*>(ky), yy, p->st));
+  std::vector<double> h(3 * (size_t)S);
+  T2SH_CK(cudaMemcpyAsync(h.data(), p->obj, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, p->st));
+  T2SH_CK(cudaStreamSynchronize(p->st));
+  for (int i = 0; i < S; ++i) {
+    out[2 * i] = 0.5 * h[i] - h[S + i];
+    out[2 * i + 1] = kform == T2SH_KSPACE_TE ? 0.5 * h[2 * S + i] : std::nan("");
+  }
+  return T2SH_OK;
 }
 
 }  // extern "C"

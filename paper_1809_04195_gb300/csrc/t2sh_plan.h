@@ -110,6 +110,8 @@ cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alp
 cudaError_t launch_cg_init(const Geom& g, const float2* x, const float2* w, const float2* aty, const float2* v,
                            const float2* u, float rho, float2* r, float2* p, double* rr, cudaStream_t st);
 cudaError_t launch_cg_dot(const Geom& g, const float2* p, const float2* w, float rho, double* pq, cudaStream_t st);
+// out[s] += sum of P_t(n) |y|^2 over T-form k-space y [S][C][T][ny][nz]
+cudaError_t launch_masked_energy(const Geom& g, const uint8_t* mask, const float2* y, double* out, cudaStream_t st);
 cudaError_t launch_cg_step(const Geom& g, float2* x, float2* r, const float2* p, const float2* w, float rho,
                            const double* rr, const double* pq, double* rr_new, cudaStream_t st);
 cudaError_t launch_cg_dir(const Geom& g, const float2* r, float2* p, const double* rr, const double* rr_new,

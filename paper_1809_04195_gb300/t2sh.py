@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
             "t2sh_llr_prox": [_vp, _vp, _f32, _i32, _i32],
             "t2sh_solve": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
             "t2sh_solve_admm": [_vp, _vp, _i32, _vp, _f32, _i32, ctypes.POINTER(ctypes.c_double)],
+            "t2sh_objective": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
             "t2sh_postprocess": [_vp, _vp, ctypes.POINTER(_i32), _i32, _f32, _vp],
             "t2sh_coil_compression": [ctypes.POINTER(Sparse), _vp, _i32, _i32, _vp, _vp],
             "t2sh_preprocess": [ctypes.POINTER(Sparse), _vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp],
@@ -345,6 +346,16 @@ class Plan:
             rp = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         _check(lib().t2sh_solve_admm(self._h, kp, kform, op, float(rho), int(cg_iters), rp))
         return (out, res) if residual else out
+
+    def objective(self, kspace, kform, x):
+        """Data term of Eq. 5 at x per slice, as (h, c) float64 arrays [S] with f = h + c:
+        h = 1/2 <x, A^H A x> - Re <x, A^H y>, c = 1/2 ||P y||^2 (NaN for projected k-space)."""
+        import torch
+        kp = _ptr(kspace, torch.complex64, self._kshape(kform), self.host_io)
+        xp = _ptr(x, torch.complex64, self.vec_shape, self.host_io)
+        out = np.zeros((self.S, 2), np.float64)
+        _check(lib().t2sh_objective(self._h, kp, kform, xp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out[:, 0], out[:, 1]
 
     def postprocess(self, alpha, te_index, pf: float = 0.65, out=None):
         """TE images [S][nte][ny][nz] (float32, device): back-projection at the echoes
