@@ -27,7 +27,10 @@ struct ColTma {
   static constexpr int SF = ExLayout<R1>::SF;  // forward in-line stride (odd)
   static constexpr int SI = 17;                // inverse in-line stride (odd)
   static constexpr int LINE = ExLayout<R1>::LINE;
-  static constexpr int LS = LINE + ((18 - LINE % 16) % 16);  // = 2 (mod 16)
+  // a half-warp holds W columns x JPH = 16 / W consecutive j; the exchange line stride
+  // LS = JPH (mod 16) with SF = 1 (mod 16) spreads its accesses over all banks
+  static constexpr int JPH = 16 / W;
+  static constexpr int LS = LINE + ((16 + JPH - LINE % 16) % 16);
   static constexpr size_t off_ex = ((size_t)N * 8 + 127) / 128 * 128;                       // bytes
   static constexpr size_t off_t = (off_ex + (size_t)4 * W * LS * 8 + 127) / 128 * 128;
   static constexpr size_t off_psi = off_t + (size_t)4 * N * W * 8;
@@ -48,8 +51,9 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
   float* ps = reinterpret_cast<float*>(smem_raw + CT::off_psi);    // [p][y][W] (TMA box)
   const int nz = g.nz, NN = N * nz, K = g.K, P = g.P;
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + (size_t)P * N * W * 4);
-  const int w = threadIdx.x & (W - 1), jl = (threadIdx.x >> WL) & 1, k = (threadIdx.x >> (WL + 1)) & 3,
-            j = 2 * (threadIdx.x >> (WL + 3)) + jl;
+  constexpr int JPH = CT::JPH;
+  const int w = threadIdx.x & (W - 1), jl = (threadIdx.x >> WL) & (JPH - 1), k = (threadIdx.x >> 4) & 3,
+            j = JPH * (threadIdx.x >> 6) + jl;
   const bool live = k < K;
   const unsigned bytes_t = (unsigned)(K * N * W * 8), bytes_p = (unsigned)(P * N * W * 4);
   if (threadIdx.x == 0) {
