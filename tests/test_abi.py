@@ -60,6 +60,10 @@ def test_workspace_bytes_formula(lib):
     (dict(precision=2), t2sh.EINVAL),     # neither FP32 nor MIXED_BF16
     (dict(flags=0x80), t2sh.EINVAL),
     (dict(flags=0x10), t2sh.EINVAL),
+    (dict(ny=1024), t2sh.EINVAL),        # above the largest slice matrix, 512
+    (dict(block=17), t2sh.EINVAL),       # above the largest block, 16
+    # an LLR band of K x b x nz = 4 x 16 x 512 complex values (262 KB) exceeds shared memory
+    (dict(ny=512, nz=512, block=16), t2sh.EUNSUPPORTED),
 ])
 def test_invalid_dims_rejected(lib, kw, status):
     base = dict(ny=64, nz=48, ncoils=8, nechoes=32, nbasis=4, nslices=1, block=8, iters=10)
@@ -68,6 +72,14 @@ def test_invalid_dims_rejected(lib, kw, status):
     n = ctypes.c_size_t(0)
     assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == status
     assert len(t2sh.last_error()) > 0
+
+
+def test_largest_supported_shapes_accepted(lib):
+    """512 x 512 with a band that fits: K = 4 with 8-row blocks, K = 2 with 16-row blocks."""
+    for kw in (dict(nbasis=4, block=8), dict(nbasis=2, block=16)):
+        d = t2sh.make_dims(512, 512, 2, 8, nslices=1, iters=4, **kw)
+        n = ctypes.c_size_t(0)
+        assert lib.t2sh_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == t2sh.OK
 
 
 def test_paper_slice_matrix_accepted(lib):

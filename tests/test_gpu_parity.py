@@ -87,6 +87,10 @@ SHAPES = [
     (1, 192, 192, 2, 12, 4, 2),  # two map sets on the specialised passes
     (2, 96, 64, 2, 8, 2, 1),     # K = 2 on the specialised passes
     (1, 260, 240, 7, 16, 4, 2),  # Table I slice matrix: radix-13 passes, C = 7, M = 2
+    (1, 512, 512, 2, 8, 4, 1),   # the largest slice matrix (generic passes)
+    (1, 32, 24, 2, 16, 8, 1),    # K = 8, the largest basis
+    (2, 8, 8, 1, 4, 2, 1),       # the smallest matrix, one coil
+    (1, 26, 52, 2, 8, 3, 1),     # radix 13 on the generic passes
 ]
 
 
@@ -142,6 +146,9 @@ def test_step_matches_oracle(T):
     (48, 30, 8, 1, 6, 1, 6),    # K > 4
     (256, 160, 8, 0, 0, 1, 4),
     (260, 240, 12, 7, 11, 2, 4),  # Table I: 12 x 12 blocks, 260 mod 12 = 8, two map sets
+    (8, 8, 16, 13, 9, 1, 2),      # a block larger than the image: shifts beyond its size
+    (512, 512, 16, 15, 7, 1, 2),  # the largest matrix and block (K = 2: the band fits shared memory)
+    (32, 24, 8, 5, 3, 1, 8),      # K = 8
 ])
 def test_llr_prox_matches_oracle(T, ny, nz, b, sy, sz, M, K):
     rng, phi, mask, maps = random_problem(ny * nz + b, 2, ny, nz, 2, max(K, 8), K, M)
@@ -157,6 +164,17 @@ def test_llr_prox_matches_oracle(T, ny, nz, b, sy, sz, M, K):
     for s in range(2):
         ref = O.llr_prox(xs[s], b, tau, sy, sz)
         assert nrmse(got[s], ref) < OP_TOL
+
+
+def test_solve_largest_matrix(T):
+    """512 x 512 slice, K = 4, 8 x 8 blocks, a few iterations against the oracle."""
+    rng, phi, mask, maps = random_problem(512, 1, 512, 512, 2, 8, 4, 1)
+    y = crandn(rng, 1, 2, 8, 512, 512) * mask[None, None] * 0.1
+    with make_plan(T, phi, mask, maps, block=8, lam=0.02, iters=4, seed=9) as p:
+        got = host(p.solve(c64(y), T.KSPACE_TE))
+        p.sync()
+    ref = O.fista(y[0].astype(np.complex64).astype(np.complex128), "te", maps[0], mask, phi, 0.02, 8, 4, 9)
+    assert nrmse(got[0], ref) < SOLVE_TOL
 
 
 def test_llr_prox_limits(T):
