@@ -11,7 +11,9 @@
 //                      -> x[j + 16 k] (k < R1).
 // The row pass (kz) keeps each line in one half-warp, so global loads of a row are
 // 128-byte runs; the column pass (ky) puts the 8 columns of a tile on adjacent lanes.
-// Both stream their next inputs into shared memory with cp.async while computing.
+// The column pass and the row pass's map rows stream into shared memory with cp.async while
+// the previous tile or coil is transformed; the adjoint row pass reads its t rows straight
+// from global memory into registers (a half-warp reads 16 consecutive values).
 #include <algorithm>
 
 #include "t2sh_device.cuh"
@@ -27,7 +29,10 @@ using Ex = ExLayout<R1>;
 // two rows (128 threads) and the kernel is held to 64 registers (forward, eight CTAs per
 // SM) or 80 (adjoint, six): many small CTAs keep the SM issuing while others wait at
 // their per-coil barriers (forward 1.47 -> 1.18 ms on the knee scan against bands of 8
-// rows).  N >= 240 and two map sets keep bands of 4 rows without a block bound.
+// rows).  N >= 240 and two map sets keep bands of 4 rows without a block bound.  The
+// adjoint reads t straight into registers instead of staging it by cp.async (knee
+// 1.51 -> 1.31 ms, Table I shape 2.30 -> 1.52 ms): the staging cost more instructions
+// than the latency it hid.
 // ------------------------------------------------------------------------------------
 // Padded strides (float2) of the row pass's exchange lines (LX) and staged map rows (MS).
 // The packed second stage reads R1 consecutive items from each of several lines per
@@ -56,9 +61,7 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
                                               float2* __restrict__ t, float2* __restrict__ out) {
   constexpr int R1 = N / 16;
   constexpr int LINE = RowPad<N>::LX;
-  // the adjoint keeps unpadded map rows: at N = 160 the padding would cost it its third
-  // CTA per SM (76.9 KB of shared memory against 76.8 KB)
-  constexpr int MS = (MODE == ROW_ADJ) ? N : RowPad<N>::MS;
+  constexpr int MS = RowPad<N>::MS;
   constexpr int SF = Ex<R1>::SF;
   extern __shared__ float2 smem[];
   const int NN = g.ny * N, K = g.K, M = g.M;
@@ -69,14 +72,13 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
   const int L = threadIdx.x >> 4;  // line: k * RB + r
   const int k = L / kRowRB, r = L - k * kRowRB;
   const bool live = (k < K) && (r < rb);
-  // shared memory: twiddles | exchange [NL][LINE] | maps stage x2 [MC][RB][MS] | t stage x2 [NL][N]
+  // shared memory: twiddles | exchange [NL][LINE] | maps stage x2 [MC][RB][MS]
   float2* tw = smem;
   float2* ex = tw + N;
   float2* mst = ex + NL * LINE;
-  float2* tst = mst + 2 * MC * kRowRB * MS;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
 
-  // 16-byte copies of the coil's map rows (and, for the adjoint, its t rows) walked over
+  // 16-byte copies of the coil's map rows walked over
   // (plane, row < RB, column pair) with compile-time divisors; rows past a partial band's
   // end are skipped
   auto issue = [&](int c, int buf) {
@@ -87,15 +89,6 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
       const int line = e2 / H, col = 2 * (e2 - line * H);
       const int m = line / kRowRB, row = line - m * kRowRB;
       if (row < rb) cp_async16(md + line * MS + col, mp + (long long)m * NN + row * N + col);
-    }
-    if (MODE == ROW_ADJ) {
-      const float2* tp = t + ((long long)(s * g.C + c) * K) * NN + (long long)y0 * N;
-      float2* td = tst + buf * NL * N;
-      for (int e2 = threadIdx.x; e2 < K * kRowRB * H; e2 += blockDim.x) {
-        const int line = e2 / H, col = 2 * (e2 - line * H);
-        const int kk = line / kRowRB, row = line - kk * kRowRB;
-        if (row < rb) cp_async16(td + line * N + col, tp + (long long)kk * NN + row * N + col);
-      }
     }
   };
   issue(0, 0);
@@ -144,9 +137,10 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
       }
       dft_r<R1, false>(a);
     } else {
-      const float2* trow = tst + buf * NL * N + L * N;
+      // t straight from global memory: a half-warp reads 16 consecutive values per q
+      const float2* trow = t + ((long long)(s * g.C + c) * K + k) * NN + (long long)(y0 + r) * N;
 #pragma unroll
-      for (int q = 0; q < R1; ++q) a[q] = trow[j + 16 * q];
+      for (int q = 0; q < R1; ++q) a[q] = live ? trow[j + 16 * q] : make_float2(0.f, 0.f);
       dft_r<R1, true>(a);
     }
 #pragma unroll
@@ -367,9 +361,9 @@ constexpr int kColW = 8;  // columns per tile of the column pass
 template <int N, int MODE, int MC>
 static size_t row_fast_smem() {
   constexpr int R1 = N / 16, RB = RowFastRB<N, MC, MODE>::value, NL = 4 * RB;
-  constexpr int MS = (MODE == ROW_ADJ) ? N : RowPad<N>::MS;
+  constexpr int MS = RowPad<N>::MS;
   return sizeof(float2) * ((size_t)N + NL * RowPad<N>::LX + 2 * (size_t)MC * RB * MS +
-                           (MODE == ROW_ADJ ? 2 * (size_t)NL * N : 0));
+                           0);
 }
 
 template <int N, int MODE, int MC>
