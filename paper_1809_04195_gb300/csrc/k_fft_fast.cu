@@ -27,12 +27,13 @@ using Ex = ExLayout<R1>;
 // Row pass.  CTA = (slice, band of RB rows), 16 x 4 x RB threads, thread
 // (j, line = k * RB + r).  K <= 4, M <= 2.  With one map set and N < 240 the bands are
 // two rows (128 threads) and the kernel is held to 64 registers (forward, eight CTAs per
-// SM) or 80 (adjoint, six): many small CTAs keep the SM issuing while others wait at
+// SM) or 96 (adjoint, five): many small CTAs keep the SM issuing while others wait at
 // their per-coil barriers (forward 1.47 -> 1.18 ms on the knee scan against bands of 8
 // rows).  N >= 240 and two map sets keep bands of 4 rows without a block bound.  The
 // adjoint reads t straight into registers instead of staging it by cp.async (knee
 // 1.51 -> 1.31 ms, Table I shape 2.30 -> 1.52 ms): the staging cost more instructions
-// than the latency it hid.
+// than the latency it hid.  On two-row bands the next coil's values are loaded one coil
+// ahead (1.31 -> 1.28 ms).
 // ------------------------------------------------------------------------------------
 // Padded strides (float2) of the row pass's exchange lines (LX) and staged map rows (MS).
 // The packed second stage reads R1 consecutive items from each of several lines per
@@ -52,7 +53,7 @@ template <int N, int MC, int MODE>
 struct RowFastRB {
   static constexpr bool small = MC == 1 && N < 240;  // two-row bands, occupancy-bounded kernel
   static constexpr int value = small ? 2 : 4;
-  static constexpr int min_blocks = MODE == ROW_FWD ? 8 : 6;
+  static constexpr int min_blocks = MODE == ROW_FWD ? 8 : 5;
 };
 
 template <int N, int MODE, int MC, int kRowRB = RowFastRB<N, MC, MODE>::value>
@@ -118,6 +119,15 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
   const bool liveb = (kPack ? ((int)threadIdx.x < NL * R1) : (j < R1)) && kb < K && rbb < rb;
   const float2* exb = ex + Lb * LINE;
 
+  // adjoint on two-row bands: the next coil's t values are requested one coil ahead, into
+  // registers (the four-row kernel has no registers to spare for them)
+  constexpr bool kPrefetchT = MODE == ROW_ADJ && RowFastRB<N, MC, MODE>::small;
+  float2 tn[kPrefetchT ? R1 : 1];
+  if constexpr (kPrefetchT) {
+    const float2* trow = t + ((long long)(s * g.C) * K + k) * NN + (long long)(y0 + r) * N;
+#pragma unroll
+    for (int q = 0; q < R1; ++q) tn[q] = live ? trow[j + 16 * q] : make_float2(0.f, 0.f);
+  }
   for (int c = 0; c < g.C; ++c) {
     const int buf = c & 1;
     if (c + 1 < g.C) issue(c + 1, buf ^ 1);
@@ -138,9 +148,19 @@ __device__ __forceinline__ void row_fast_body(const Geom& g, const float2* __res
       dft_r<R1, false>(a);
     } else {
       // t straight from global memory: a half-warp reads 16 consecutive values per q
-      const float2* trow = t + ((long long)(s * g.C + c) * K + k) * NN + (long long)(y0 + r) * N;
+      if constexpr (kPrefetchT) {
 #pragma unroll
-      for (int q = 0; q < R1; ++q) a[q] = live ? trow[j + 16 * q] : make_float2(0.f, 0.f);
+        for (int q = 0; q < R1; ++q) a[q] = tn[q];
+        if (c + 1 < g.C) {
+          const float2* trow = t + ((long long)(s * g.C + c + 1) * K + k) * NN + (long long)(y0 + r) * N;
+#pragma unroll
+          for (int q = 0; q < R1; ++q) tn[q] = live ? trow[j + 16 * q] : make_float2(0.f, 0.f);
+        }
+      } else {
+        const float2* trow = t + ((long long)(s * g.C + c) * K + k) * NN + (long long)(y0 + r) * N;
+#pragma unroll
+        for (int q = 0; q < R1; ++q) a[q] = live ? trow[j + 16 * q] : make_float2(0.f, 0.f);
+      }
       dft_r<R1, true>(a);
     }
 #pragma unroll
