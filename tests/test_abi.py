@@ -101,3 +101,19 @@ def test_null_arguments_rejected(lib):
     assert lib.t2sh_workspace_bytes(None, None) == t2sh.EINVAL
     assert lib.t2sh_normal_op(None, None, None) == t2sh.EINVAL
     assert lib.t2sh_destroy(None) == t2sh.OK
+    out = ctypes.c_void_p(0)
+    assert lib.t2sh_plan(None, None, None, None, None, ctypes.byref(out)) == t2sh.EINVAL and not out.value
+    assert lib.t2sh_forward(None, None, None, t2sh.KSPACE_TE) == t2sh.EINVAL
+    assert lib.t2sh_adjoint(None, None, t2sh.KSPACE_TE, None) == t2sh.EINVAL
+    assert lib.t2sh_llr_prox(None, None, 0.1, 0, 0) == t2sh.EINVAL
+    assert lib.t2sh_solve(None, None, t2sh.KSPACE_PROJ, None, None) == t2sh.EINVAL
+    assert lib.t2sh_solve_admm(None, None, t2sh.KSPACE_PROJ, None, 1.0, 3, None) == t2sh.EINVAL
+    assert lib.t2sh_objective(None, None, t2sh.KSPACE_PROJ, None, None) == t2sh.EINVAL
+    assert lib.t2sh_postprocess(None, None, None, 0, 0.65, None) == t2sh.EINVAL
+    assert lib.t2sh_sync(None) == t2sh.EINVAL
+    assert lib.t2sh_configure(None, 0, 0) == t2sh.EINVAL
+    assert lib.t2sh_wait_selftest(None, 1000) == t2sh.EINVAL
+    assert lib.t2sh_autotune(None, 3, None, None) == t2sh.EINVAL
+    assert lib.t2sh_solve_begin(None, None, t2sh.KSPACE_PROJ) == t2sh.EINVAL
+    assert lib.t2sh_solve_iterate(None, 1, None) == t2sh.EINVAL
+    assert lib.t2sh_solve_end(None, None, None) == t2sh.EINVAL
