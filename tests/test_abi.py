@@ -28,6 +28,52 @@ def test_exports_every_declared_symbol(lib):
         assert getattr(lib, s) is not None
 
 
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "t2sh.h"
+int main(void) {
+  t2sh_dims d = {0};
+  d.ny = 256; d.nz = 160; d.ncoils = 12; d.nmaps = 1; d.nechoes = 80; d.nbasis = 4;
+  d.nslices = 320; d.block = 8; d.lambda = 0.005f; d.iters = 100; d.seed = 1; d.precision = T2SH_FP32;
+  size_t ws = 0;
+  int32_t sh[4];
+  if (t2sh_workspace_bytes(&d, &ws) != T2SH_OK) { fprintf(stderr, "%s\n", t2sh_last_error()); return 1; }
+  if (t2sh_shifts(1809, 2, 8, sh) != T2SH_OK) return 2;
+  d.ny = 63;
+  if (t2sh_workspace_bytes(&d, &ws) == T2SH_OK) return 3;
+  printf("%d %zu %d %d %d %d\n", t2sh_version(), ws, sh[0], sh[1], sh[2], sh[3]);
+  return 0;
+}
+"""
+
+
+def test_header_is_c99_and_links_from_c(lib, tmp_path):
+    """A plain C99 program (-pedantic -Werror) includes the header, links the library and
+    gets the same host-only results as the binding and the oracle."""
+    import os
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "main.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "main"
+    libdir = os.path.dirname(t2sh.LIB_PATH)
+    inc = os.path.join(os.path.dirname(libdir), "include")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src),
+                        "-L", libdir, "-l:libt2sh.so", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ)
+    env["LD_LIBRARY_PATH"] = os.pathsep.join(p for p in ("/usr/local/cuda/lib64", env.get("LD_LIBRARY_PATH", "")) if p)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env)
+    assert r.returncode == 0, r.stderr
+    ver, ws, *sh = (int(v) for v in r.stdout.split())
+    assert ver == t2sh.version()
+    assert ws == t2sh.workspace_bytes(t2sh.make_dims(256, 160, 12, 80, 4, nslices=320, block=8, iters=100,
+                                                     lam=0.005, seed=1))
+    assert sh == [int(v) for v in O.llr_shifts(1809, 2, 8).ravel()]
+
+
 def test_version(lib):
     assert t2sh.version() == 100
 
