@@ -14,7 +14,9 @@ on one GPU with real reconstructions:
   next tick boundary and finished scans leave (continuous batching);
 * a virtual clock advances by the measured GPU time of every tick and jumps over idle
   gaps, so arrival rates of minutes per scan need no waiting.  Latency = completion
-  time - arrival time on that clock.
+  time - arrival time on that clock;
+* a scan can be withdrawn (cancel): a queued one leaves the queue, a resident one has
+  its plan closed and its memory returned at the next tick boundary.
 
 Every step of a reconstruction runs in libt2sh (t2sh_solve_begin / _iterate / _end);
 this module only schedules.
@@ -44,6 +46,7 @@ class ScanRequest:
     # filled in by the server
     admitted_s: float = -1.0
     done_s: float = -1.0
+    cancelled_s: float = -1.0
     result: object = None
     plan: object = field(default=None, repr=False)
     stream: object = field(default=None, repr=False)
@@ -83,6 +86,8 @@ class Server:
         self.queue: list[ScanRequest] = []
         self.active: list[ScanRequest] = []
         self.done: list[ScanRequest] = []
+        self.cancelled: list[ScanRequest] = []
+        self.cancel_requests: list[tuple[float, int]] = []
         self.now = 0.0
         self.used = 0
         self.busy_s = 0.0
@@ -95,6 +100,33 @@ class Server:
             raise ValueError(f"scan {req.scan_id} needs {req.footprint} bytes, budget {self.budget}")
         self.queue.append(req)
         self.queue.sort(key=lambda r: (r.arrival_s, r.scan_id))
+
+    def cancel(self, scan_id: int, at_s: float = 0.0):
+        """Withdraw scan `scan_id` at virtual time at_s (applied at the first tick boundary
+        at or after it).  A scan that has already finished by then is left alone."""
+        self.cancel_requests.append((float(at_s), int(scan_id)))
+        self.cancel_requests.sort()
+
+    def _apply_cancellations(self):
+        while self.cancel_requests and self.cancel_requests[0][0] <= self.now:
+            _, sid = self.cancel_requests.pop(0)
+            for i, r in enumerate(self.queue):
+                if r.scan_id == sid:
+                    self.queue.pop(i)
+                    r.cancelled_s = self.now
+                    self.cancelled.append(r)
+                    break
+            else:
+                for r in self.active:
+                    if r.scan_id == sid:
+                        r.stream.synchronize()
+                        r.plan.close()
+                        r.plan = None
+                        r.cancelled_s = self.now
+                        self.used -= r.footprint
+                        self.active.remove(r)
+                        self.cancelled.append(r)
+                        break
 
     def _admit(self):
         # FCFS: the head of the queue goes first; a later scan never overtakes it
@@ -136,6 +168,9 @@ class Server:
 
     def run(self):
         while self.queue or self.active:
+            self._apply_cancellations()
+            if not (self.queue or self.active):
+                break
             self._admit()
             if not self.active:
                 self.now = max(self.now, self.queue[0].arrival_s)  # idle: jump to the next arrival
@@ -148,7 +183,7 @@ class Server:
         wait = np.array([r.admitted_s - r.arrival_s for r in self.done])
         slices = sum(r.dims.nslices for r in self.done)
         span = max(r.done_s for r in self.done) - min(r.arrival_s for r in self.done) if self.done else 0.0
-        return {"scans": len(self.done), "slices": int(slices),
+        return {"scans": len(self.done), "cancelled": len(self.cancelled), "slices": int(slices),
                 "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
                 "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
                 "latency_max_s": float(lat.max()) if len(lat) else None,

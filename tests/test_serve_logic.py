@@ -24,6 +24,7 @@ class FakeLib:
 
     def __init__(self, clock, cost_per_iter):
         self.clock, self.cost = clock, cost_per_iter
+        self.closed = []
         lib = self
 
         class Plan:
@@ -43,7 +44,7 @@ class FakeLib:
                 return ("result", self.dims.tag)
 
             def close(self):
-                pass
+                lib.closed.append(self.dims.tag)
 
         self.Plan = Plan
 
@@ -147,3 +148,29 @@ def test_oversize_scan_is_refused(monkeypatch):
     srv, lib, _ = make_server(monkeypatch, budget=5000)
     with pytest.raises(ValueError):
         srv.submit(req(lib, 0, 0.0, 10, 10**6))
+
+
+def test_cancel_queued_and_resident_scans(monkeypatch):
+    """A queued scan withdrawn before admission never runs; a resident one is closed at the
+    next tick boundary and its memory admits the waiting scan; cancelling a finished or
+    unknown scan changes nothing."""
+    per = footprint(dims(0, 10, 1000))
+    srv, lib, _ = make_server(monkeypatch, budget=2 * per + 100, cost=0.01, iters_per_tick=10)
+    srv.submit(req(lib, 0, 0.0, 40, 1000))
+    srv.submit(req(lib, 1, 0.0, 40, 1000))
+    srv.submit(req(lib, 2, 0.05, 10, 1000))   # waits: the budget holds two scans
+    srv.submit(req(lib, 3, 0.06, 10, 1000))   # waits behind scan 2
+    srv.cancel(3, at_s=0.1)                   # still queued then
+    srv.cancel(1, at_s=0.15)                  # resident: leaves at the tick boundary 0.2
+    srv.cancel(0, at_s=10.0)                  # finished long before
+    srv.cancel(99, at_s=0.0)                  # unknown
+    rep = srv.run()
+    done = {r.scan_id: r for r in srv.done}
+    gone = {r.scan_id: r for r in srv.cancelled}
+    assert sorted(done) == [0, 2] and sorted(gone) == [1, 3]
+    assert gone[3].admitted_s == -1.0 and gone[3].cancelled_s == pytest.approx(0.2)
+    assert gone[1].cancelled_s == pytest.approx(0.2) and gone[1].result is None
+    assert 1 in lib.closed and 3 not in lib.closed
+    assert done[2].admitted_s == pytest.approx(0.2)        # admitted into the freed memory
+    assert srv.resident[:3] == [[0, 1], [0, 2], [0]]
+    assert rep["scans"] == 2 and rep["cancelled"] == 2 and srv.used == 0
