@@ -625,3 +625,47 @@ def test_calibration_average_over_echoes():
     assert cal.shape == (Ctot, w, w, w)
     assert np.all(cal[:, :, 2, 3] == 2.0)        # (ky, kz) = (4, 5) -> window (2, 3)
     assert np.count_nonzero(cal) == Ctot * w      # only that point, all w kx samples
+
+
+# ----------------------------------------------------------------------------------
+# direct pins of the helpers the composite functions use
+# ----------------------------------------------------------------------------------
+def test_llr_norm_brute_force_blocks():
+    """sum_n ||R_n alpha||_* with blocks cut by explicit index sets: rows (sy + i b + r) mod Ny,
+    columns likewise, the last block partial, one matrix per map set; nuclear norms by
+    numpy's matrix norm."""
+    rng = np.random.default_rng(41)
+    M, K, Ny, Nz, b, sy, sz = 2, 3, 6, 5, 4, 3, 2
+    a = crandn(rng, M, K, Ny, Nz)
+    total = 0.0
+    for m in range(M):
+        for i0 in range(0, Ny, b):
+            rows = [(sy + i0 + r) % Ny for r in range(min(b, Ny - i0))]
+            for j0 in range(0, Nz, b):
+                cols = [(sz + j0 + c) % Nz for c in range(min(b, Nz - j0))]
+                X = np.array([[a[m, k, y, z] for k in range(K)] for y in rows for z in cols])
+                total += np.linalg.norm(X, "nuc")
+    assert abs(O.llr_norm(a, b, sy, sz) - total) < 1e-12 * total
+
+
+def test_adjoint_data_forms_agree_and_reject_unknown():
+    phi, maps, mask, rng = tiny_problem(43)
+    y = crandn(rng, 2, 6, 8, 8)
+    te = O.adjoint_data(y, "te", maps, mask, phi)
+    pr = O.adjoint_data(O.project(y, mask, phi), "proj", maps, mask, phi)
+    assert np.abs(te - pr).max() < 1e-12 * np.abs(te).max()
+    with pytest.raises(ValueError):
+        O.adjoint_data(y, "raw", maps, mask, phi)
+
+
+def test_sense_pair_is_adjoint_and_backprojection_round_trips():
+    phi, maps, mask, rng = tiny_problem(44, M=2)
+    x = crandn(rng, 2, 3, 8, 8)
+    yc = crandn(rng, 2, 3, 8, 8)
+    lhs = np.vdot(yc, O.sense(x, maps))
+    rhs = np.vdot(O.sense_adj(yc, maps), x)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    alpha = crandn(rng, 2, 2, 8, 8)
+    xt = O.backproject(alpha, phi)                     # [M][T][..]
+    back = np.einsum("tk,mt...->mk...", phi, xt)       # Phi^T x with orthonormal columns
+    assert np.abs(back - alpha).max() < 1e-12 * np.abs(alpha).max()
