@@ -1,0 +1,64 @@
+"""CPU checks of bench.py's reporting: the reference arm's JSON line (the FP64 oracle on
+the host, no GPU), silence on ranks other than 0, the clock record's throttle reasons,
+and the algorithmic bytes behind the roofline figures."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def run_bench(args, env_extra=None):
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                          env=env, cwd=ROOT, timeout=600)
+
+
+def test_reference_arm_json_line():
+    r = run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"] and d["vs_baseline"] is None
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    r = run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_clock_record_reasons():
+    c = bench.Clocks(0)
+    idle = "0, 1005, 2070, 160.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    load = ["0, 2070, 2070, 990.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1010.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1900, 2070, 1000.0, 0x8, Active, Not Active, Not Active, Not Active"]
+    c.out = "\n".join([idle] + load)
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    c.out = ""
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_algorithmic_bytes_of_the_knee_scan():
+    """Bytes per launch on the knee scan (S=320, C=12, M=1, K=4, N=256x160), as the kernel
+    table states them: row passes 6.71 GB, column pass 10.07 GB, LLR + FISTA 2.52 GB."""
+    ab = bench.algorithmic_bytes(320, 12, 1, 4, 256 * 160)
+    assert ab["row_fwd"] == ab["row_adj"] == pytest.approx(6.71e9, rel=2e-3)
+    assert ab["col"] == pytest.approx(10.07e9, rel=2e-3)
+    assert ab["llr"] == pytest.approx(2.52e9, rel=2e-3)
