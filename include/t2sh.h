@@ -392,13 +392,35 @@ t2sh_status t2sh_timing_read(t2sh_plan_t plan, int32_t kernel_class, int64_t* la
  * device current; make that first call before any stream capture.  Every call reuses
  * the same array and overwrites what the previous call left there, so calls that
  * overlap on the GPU (different streams, or threads without ordering) race: serialise
- * them.  Asynchronous on the stream.
+ * them.  Asynchronous on the stream: the status says only that the work was queued.
+ * Like the planned operator, the kernels bound every wait on a tile copy or tensor-core
+ * operation (2 s); a wait that runs out sets a flag in the array, which stays set across
+ * later calls until t2sh_noalloc_sync reads and clears it.  Call t2sh_noalloc_sync before
+ * trusting y.
  */
 t2sh_status t2sh_normal_op_noalloc(const t2sh_dims* dims, const float* phi, const uint8_t* mask,
                                    const void* maps, const void* x, void* y, void* stream);
 
 /* Size in bytes of the static scratch array behind t2sh_normal_op_noalloc. */
 size_t t2sh_noalloc_scratch_bytes(void);
+
+/*
+ * t2sh_noalloc_sync -- synchronise `stream` (cudaStream_t, NULL: default stream) and
+ * report whether a bounded device wait of t2sh_normal_op_noalloc ran out on the current
+ * device since the last t2sh_noalloc_sync: T2SH_ETIMEOUT if it did (the flag is then
+ * cleared, and the y of the call that timed out is not valid), T2SH_ECUDA for a CUDA
+ * error, else T2SH_OK.  Allocates nothing.  The paper has no counterpart.
+ */
+t2sh_status t2sh_noalloc_sync(void* stream);
+
+/*
+ * t2sh_noalloc_wait_selftest -- exercises that failure path without a fault: one kernel
+ * on `stream` waits, through the bounded wait the tile kernels use, on a barrier that
+ * nothing completes, gives up after limit_ns (1 .. 1e9 ns) and sets the flag of the
+ * static array; the next t2sh_noalloc_sync returns T2SH_ETIMEOUT.  The paper has no
+ * counterpart.
+ */
+t2sh_status t2sh_noalloc_wait_selftest(uint64_t limit_ns, void* stream);
 
 /* Message of the last failing call on this thread ("" if none).  Never NULL. */
 const char* t2sh_last_error(void);

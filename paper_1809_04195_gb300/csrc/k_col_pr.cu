@@ -175,19 +175,12 @@ __global__ void __launch_bounds__(W * 4 * P, 2) k_col_pr(Geom g, const float2* _
 template <int P, int R1, int W>
 cudaError_t col_pr_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
   using CP = ColPR<P, R1, W>;
-  static int nsm = 0, per = 0;
-  if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_pr<P, R1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)CP::smem(10));
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_pr<P, R1, W>, CP::THREADS, CP::smem(10))) !=
-        cudaSuccess)
-      return e;
-    if (per < 1) per = 1;
-  }
+  int nsm = 0, per = 0;
+  const void* kern = (const void*)k_col_pr<P, R1, W>;
+  cudaError_t e = smem_optin(kern, (int)CP::smem(10));
+  if (e == cudaSuccess) e = sm_count(&nsm);
+  if (e == cudaSuccess) e = ctas_per_sm(kern, CP::THREADS, CP::smem(10), &per);
+  if (e != cudaSuccess) return e;
   const int ntz = g.nz / W;
   const long long ntiles = (long long)g.S * g.C * ntz;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;

@@ -358,13 +358,11 @@ cudaError_t col_tc_go(const Geom& g, const float2* tw, const float* psi, float2*
   if (enc(&tm_t, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, t, dt, st_t, bt, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorNotSupported;
-  static int nsm = 0;
-  if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_tc<R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::smem);
+  int nsm = 0;
+  {
+    cudaError_t e = smem_optin((const void*)k_col_tc<R1>, (int)CT::smem);
+    if (e == cudaSuccess) e = sm_count(&nsm);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   }
   const int ntz = g.nz / kTcW;
   const long long ntiles = (long long)g.S * g.C * ntz;

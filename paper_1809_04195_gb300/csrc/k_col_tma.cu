@@ -250,13 +250,11 @@ cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorNotSupported;
   const size_t sm = CT::smem(g.P);
-  static int nsm = 0;
-  if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_tma<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::smem(10));
+  int nsm = 0;
+  {
+    cudaError_t e = smem_optin((const void*)k_col_tma<N, W>, (int)CT::smem(10));
+    if (e == cudaSuccess) e = sm_count(&nsm);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   }
   const int ntz = g.nz / W;
   const long long ntiles = (long long)g.S * g.C * ntz;

@@ -372,11 +372,9 @@ static cudaError_t row_go13(const Geom& g, const FftPlan& pz, const float2* tw, 
   const int RB = row_rows_per_cta(g);
   const size_t lines = (((size_t)g.K * RB * (g.nz + 1) + 1) & ~(size_t)1) * (MODE == ROW_ADJ ? 2 : 1);
   const size_t sm = sizeof(float2) * (((g.nz + 1) & ~1) + lines + 2 * (size_t)g.M * RB * g.nz);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_row<MODE, KC, MC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  {
+    const cudaError_t e = smem_optin((const void*)k_row<MODE, KC, MC, R13>, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   dim3 grid((g.ny + RB - 1) / RB, g.S);
   k_row<MODE, KC, MC, R13><<<grid, kFftThreads, sm, st>>>(g, pz, tw, maps, x, t, out, RB);
@@ -412,11 +410,9 @@ static cudaError_t col_go13(const Geom& g, const FftPlan& py, const float2* tw, 
                             const uint8_t* mask, const float2* tin, float2* tout, cudaStream_t st) {
   const int W = col_cols_per_cta(g);
   const size_t sm = sizeof(float2) * (((g.ny + 1) & ~1) + (size_t)g.K * W * (g.ny + 1));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_col<MODE, KC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  {
+    const cudaError_t e = smem_optin((const void*)k_col<MODE, KC, R13>, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   dim3 grid((g.nz + W - 1) / W, g.C, g.S);
   k_col<MODE, KC, R13><<<grid, kFftThreads, sm, st>>>(g, py, tw, psi, phi, mask, tin, tout, W);
@@ -435,20 +431,13 @@ static cudaError_t col_normal_go13(const Geom& g, const FftPlan& py, const float
                                    cudaStream_t st) {
   const int W = col_cols_per_cta(g);
   const size_t sm = sizeof(float2) * (((g.ny + 1) & ~1) + 2 * (size_t)g.K * W * (g.ny + 1));
-  static int grid_per_sm = 0;
-  static int nsm = 0;
-  if (!grid_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_normal<KC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  int grid_per_sm = 0, nsm = 0;
+  {
+    const void* kern = (const void*)k_col_normal<KC, R13>;
+    cudaError_t e = smem_optin(kern, 200 * 1024);
+    if (e == cudaSuccess) e = sm_count(&nsm);
+    if (e == cudaSuccess) e = ctas_per_sm(kern, kFftThreads, sm, &grid_per_sm);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_normal<KC, R13>, kFftThreads, sm);
-    if (e != cudaSuccess) return e;
-    grid_per_sm = per > 0 ? per : 1;
   }
   const int ntz = (g.nz + W - 1) / W;
   const long long ntiles = (long long)g.S * g.C * ntz;

@@ -396,11 +396,9 @@ static cudaError_t row_fast_go(const Geom& g, const float2* tw, const float2* ma
     if constexpr (RF::small) return k_row_fast<N, MODE, MC>;
     else return k_row_fast_wide<N, MODE, MC>;
   }();
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    const cudaError_t e = smem_optin((const void*)kern, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   dim3 grid((g.ny + RB - 1) / RB, g.S);
   kern<<<grid, 64 * RB, sm, st>>>(g, tw, maps, x, t, out);
@@ -437,18 +435,13 @@ template <int N, int W>
 static cudaError_t col_fast_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
   using CF = ColFast<N, W>;
   const size_t sm = CF::smem(g.P);
-  static int nsm = 0, per = 0;
-  if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_fast<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)CF::smem(10));
+  int nsm = 0, per = 0;
+  {
+    const void* kern = (const void*)k_col_fast<N, W>;
+    cudaError_t e = smem_optin(kern, (int)CF::smem(10));
+    if (e == cudaSuccess) e = sm_count(&nsm);
+    if (e == cudaSuccess) e = ctas_per_sm(kern, CF::THREADS, CF::smem(10), &per);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_fast<N, W>, CF::THREADS, CF::smem(10))) !=
-        cudaSuccess)
-      return e;
-    if (per < 1) per = 1;
   }
   const int ntz = g.nz / W;
   const long long ntiles = (long long)g.S * g.C * ntz;

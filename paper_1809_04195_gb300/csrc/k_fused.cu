@@ -237,11 +237,9 @@ template <int N, typename ET>
 static cudaError_t band_go(const Geom& g, const FistaArgs& a, const float2* tw, const float2* maps, float2* t,
                            float2* x, float2* z, const float2* aty, cudaStream_t st) {
   const size_t sm = band_smem<N>();
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_band_fused<N, ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    const cudaError_t e = smem_optin((const void*)k_band_fused<N, ET>, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   dim3 grid((g.ny + kBandRows - 1) / kBandRows, g.S);
   k_band_fused<N, ET><<<grid, 512, sm, st>>>(g, a, tw, maps, t, x, z, aty);

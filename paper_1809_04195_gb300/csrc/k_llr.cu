@@ -281,12 +281,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
 template <int KC, int MODE, typename ET, int MINB>
 cudaError_t llr_launch(const Geom& g, const FistaArgs& a, size_t sm, float2* x, float2* z, const float2* grad,
                        const float2* aty, float2* u, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_llr<KC, MODE, ET, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  {
+    const cudaError_t e = smem_optin((const void*)k_llr<KC, MODE, ET, MINB>, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   dim3 grid((g.ny + a.b - 1) / a.b, g.S, g.M);
   k_llr<KC, MODE, ET, MINB><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty, u);

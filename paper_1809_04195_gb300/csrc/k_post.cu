@@ -102,11 +102,9 @@ __global__ void __launch_bounds__(kPostThreads) k_post(Geom g, FftPlan pz, const
 template <int MC, bool R13>
 cudaError_t post_go(const Geom& g, const FftPlan& pz, const float2* tw_z, const float2* maps, const float* phi,
                     const float2* alpha, const PostArgs& pa, float* out, dim3 grid, size_t sm, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_post<MC, R13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  {
+    const cudaError_t e = smem_optin((const void*)k_post<MC, R13>, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   k_post<MC, R13><<<grid, kPostThreads, sm, st>>>(g, pz, tw_z, maps, phi, alpha, pa, out);
   return cudaGetLastError();

@@ -269,19 +269,15 @@ cudaError_t launch_compress_readout(const float2* lines, const float2* W, int nl
   const size_t sm = sizeof(float2) * (((nx + 1) & ~1) + (size_t)ctot * ncomp + (size_t)cb * (nx + 1));
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
   if (plan_has13(px)) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_compress_readout<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    {
+      const cudaError_t e = smem_optin((const void*)k_compress_readout<true>, 200 * 1024);
       if (e != cudaSuccess) return e;
-      attr = true;
     }
     k_compress_readout<true><<<nlines, kPpThreads, sm, st>>>(lines, W, ctot, ncomp, nx, px, tw_x, cb, yh);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_compress_readout<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    {
+      const cudaError_t e = smem_optin((const void*)k_compress_readout<false>, 200 * 1024);
       if (e != cudaSuccess) return e;
-      attr = true;
     }
     k_compress_readout<false><<<nlines, kPpThreads, sm, st>>>(lines, W, ctot, ncomp, nx, px, tw_x, cb, yh);
   }

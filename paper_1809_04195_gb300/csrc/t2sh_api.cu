@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/t2sh.h"
@@ -78,6 +79,62 @@ cudaMemPool_t stage_pool() {
   pools[dev] = pool;
   return pool;
 }
+
+std::mutex g_launch_mu;
+std::map<std::pair<const void*, int>, int> g_optin;            // (kernel, device) -> bytes
+std::map<int, int> g_nsm;                                       // device -> SMs
+std::map<std::tuple<const void*, int, int, size_t>, int> g_per; // (kernel, device, threads, smem) -> CTAs
+}  // namespace
+
+namespace t2sh {
+
+cudaError_t smem_optin(const void* kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  auto it = g_optin.find({kernel, dev});
+  if (it != g_optin.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) g_optin[{kernel, dev}] = bytes;
+  return e;
+}
+
+cudaError_t sm_count(int* n) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  auto it = g_nsm.find(dev);
+  if (it != g_nsm.end()) {
+    *n = it->second;
+    return cudaSuccess;
+  }
+  e = cudaDeviceGetAttribute(n, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) g_nsm[dev] = *n;
+  return e;
+}
+
+cudaError_t ctas_per_sm(const void* kernel, int threads, size_t smem, int* per) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  const auto key = std::make_tuple(kernel, dev, threads, smem);
+  auto it = g_per.find(key);
+  if (it != g_per.end()) {
+    *per = it->second;
+    return cudaSuccess;
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (*per < 1) *per = 1;
+  g_per[key] = *per;
+  return cudaSuccess;
+}
+}  // namespace t2sh
+
+namespace {
 
 // SplitMix64 (Steele, Lea & Flood 2014): output number i+1 of the stream from `seed`.
 uint64_t splitmix64_at(uint64_t seed, uint64_t i) {

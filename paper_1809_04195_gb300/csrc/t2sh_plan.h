@@ -138,6 +138,14 @@ bool band_fused_supported(const Geom& g, int block);
 cudaError_t launch_band_fused(const Geom& g, const FistaArgs& a, const float2* tw_z, const float2* maps, float2* t,
                               float2* x, float2* z, const float2* aty, cudaStream_t st);
 
+// Per-device launch set-up shared by the launchers (a process may drive several GPUs):
+// a kernel's dynamic shared-memory limit is raised once per (kernel, device), and the
+// SM count and a kernel's resident CTAs per SM are cached per device.  All act on the
+// current device.
+cudaError_t smem_optin(const void* kernel, int bytes);
+cudaError_t sm_count(int* n);
+cudaError_t ctas_per_sm(const void* kernel, int threads, size_t smem, int* per);
+
 int row_rows_per_cta(const Geom& g);
 int col_cols_per_cta(const Geom& g);
 

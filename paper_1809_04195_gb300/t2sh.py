@@ -91,6 +91,10 @@ def lib() -> ctypes.CDLL:
         L.t2sh_normal_op_noalloc.restype = ctypes.c_int
         L.t2sh_noalloc_scratch_bytes.argtypes = []
         L.t2sh_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.t2sh_noalloc_sync.argtypes = [_vp]
+        L.t2sh_noalloc_sync.restype = ctypes.c_int
+        L.t2sh_noalloc_wait_selftest.argtypes = [_u64, _vp]
+        L.t2sh_noalloc_wait_selftest.restype = ctypes.c_int
         L.t2sh_last_error.argtypes = []
         L.t2sh_last_error.restype = ctypes.c_char_p
         L.t2sh_version.argtypes = []
@@ -225,6 +229,24 @@ def normal_op_noalloc(dims: Dims, phi, mask, maps, x, out=None, stream=None):
 
 def noalloc_scratch_bytes() -> int:
     return int(lib().t2sh_noalloc_scratch_bytes())
+
+
+def noalloc_sync(stream=None):
+    """Synchronise the stream; raises T2shError(ETIMEOUT) if a bounded device wait of
+    normal_op_noalloc ran out since the last noalloc_sync (the flag is then cleared)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().t2sh_noalloc_sync(ctypes.c_void_p(stream.cuda_stream)))
+
+
+def noalloc_wait_selftest(limit_ns: int, stream=None):
+    """Launch a kernel whose bounded wait runs out after limit_ns and sets the flag of the
+    static array; the next noalloc_sync raises T2shError(ETIMEOUT)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().t2sh_noalloc_wait_selftest(int(limit_ns), ctypes.c_void_p(stream.cuda_stream)))
 
 
 def solve_batch(plans, kspaces, kforms=None, outs=None, stream=None):

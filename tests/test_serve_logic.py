@@ -22,17 +22,20 @@ class FakeLib:
     """Stands in for the t2sh binding: a plan iterates by advancing the clock."""
     KSPACE_TE, KSPACE_PROJ = 0, 1
 
-    def __init__(self, clock, cost_per_iter):
+    def __init__(self, clock, cost_per_iter, admit_cost=0.0, end_cost=0.0):
         self.clock, self.cost = clock, cost_per_iter
+        self.admit_cost, self.end_cost = admit_cost, end_cost
         self.closed = []
         lib = self
 
         class Plan:
             def __init__(self, dims, phi, mask, maps, stream=None):
                 self.dims, self.done = dims, 0
+                lib.clock.t += lib.admit_cost / 2
 
             def solve_begin(self, kspace, kform):
                 self.done = 0
+                lib.clock.t += lib.admit_cost / 2
 
             def solve_iterate(self, n):
                 k = min(n, self.dims.iters - self.done)
@@ -41,6 +44,7 @@ class FakeLib:
                 return self.done
 
             def solve_end(self):
+                lib.clock.t += lib.end_cost
                 return ("result", self.dims.tag)
 
             def close(self):
@@ -81,10 +85,10 @@ class CheckedServer(serve.Server):
         super()._tick()
 
 
-def make_server(monkeypatch, budget, cost=0.01, iters_per_tick=10):
+def make_server(monkeypatch, budget, cost=0.01, iters_per_tick=10, admit_cost=0.0, end_cost=0.0):
     clock = FakeClock()
     monkeypatch.setattr(serve.time, "perf_counter", clock)
-    lib = FakeLib(clock, cost)
+    lib = FakeLib(clock, cost, admit_cost, end_cost)
     return CheckedServer(lib, budget, iters_per_tick), lib, clock
 
 
@@ -174,3 +178,21 @@ def test_cancel_queued_and_resident_scans(monkeypatch):
     assert done[2].admitted_s == pytest.approx(0.2)        # admitted into the freed memory
     assert srv.resident[:3] == [[0, 1], [0, 2], [0]]
     assert rep["scans"] == 2 and rep["cancelled"] == 2 and srv.used == 0
+
+
+def test_admission_and_completion_are_charged(monkeypatch):
+    """The plan, A^H y and the result copy take GPU time too: the clock advances by them,
+    so they count in latency and busy time (0.05 s to admit, 0.02 s to finish a scan)."""
+    srv, lib, _ = make_server(monkeypatch, budget=10**9, cost=0.01, iters_per_tick=10, admit_cost=0.05,
+                              end_cost=0.02)
+    srv.submit(req(lib, 0, 0.0, 20, 1000))   # admitted at 0, ticks 0.05-0.15, 0.15-0.25, done 0.27
+    srv.submit(req(lib, 1, 0.1, 10, 1000))   # arrives in the first tick; admitted at 0.15, 0.2 s to admit
+    rep = srv.run()
+    a, b = sorted(srv.done, key=lambda r: r.scan_id)
+    assert a.admitted_s == 0.0 and b.admitted_s == pytest.approx(0.15)
+    # after b's admission (0.15 -> 0.20) the second tick runs both: 0.20 -> 0.40
+    assert a.done_s == pytest.approx(0.42)
+    assert b.done_s == pytest.approx(0.44)
+    assert b.done_s - b.arrival_s == pytest.approx(0.34)
+    assert rep["admission_s"] == pytest.approx(0.10)
+    assert rep["busy_s"] == pytest.approx(0.44)
