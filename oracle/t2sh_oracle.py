@@ -384,6 +384,92 @@ def postprocess(alpha: np.ndarray, maps: np.ndarray, phi: np.ndarray, te_index, 
 
 
 # ----------------------------------------------------------------------------------
+# Wavelet denoising (Sec. II.C after Eq. 5, and Process TE of Sec. III.C): after the
+# solve, the slices are re-joined into the volume and every basis-coefficient image gets
+# one wavelet soft-threshold.  The paper names neither the wavelet nor the threshold;
+# readings: the orthonormal Haar wavelet, a `levels`-level 3D pyramid (each level
+# transforms the previous level's approximation block along x, y and z), complex soft
+# thresholding of every detail coefficient with the threshold tau, the coarsest
+# approximation kept.  Volume axes: x = readout (slice index), y, z.
+# ----------------------------------------------------------------------------------
+def _haar_axis(blk: np.ndarray, ax: int) -> np.ndarray:
+    """One level of the orthonormal Haar analysis along axis ax: (a + b)/sqrt(2) of the
+    pairs (2i, 2i + 1) in the first half, (a - b)/sqrt(2) in the second."""
+    n = blk.shape[ax]
+    a = np.take(blk, np.arange(0, n, 2), axis=ax)
+    b = np.take(blk, np.arange(1, n, 2), axis=ax)
+    return np.concatenate([(a + b) / np.sqrt(2.0), (a - b) / np.sqrt(2.0)], axis=ax)
+
+
+def _ihaar_axis(blk: np.ndarray, ax: int) -> np.ndarray:
+    n = blk.shape[ax]
+    lo = np.take(blk, np.arange(0, n // 2), axis=ax)
+    hi = np.take(blk, np.arange(n // 2, n), axis=ax)
+    out = np.empty_like(blk)
+    idx_e = [slice(None)] * blk.ndim
+    idx_o = [slice(None)] * blk.ndim
+    idx_e[ax] = slice(0, n, 2)
+    idx_o[ax] = slice(1, n, 2)
+    out[tuple(idx_e)] = (lo + hi) / np.sqrt(2.0)
+    out[tuple(idx_o)] = (lo - hi) / np.sqrt(2.0)
+    return out
+
+
+def haar3(v: np.ndarray, levels: int) -> np.ndarray:
+    """Forward 3D Haar pyramid of v [Nx][Ny][Nz] (every size a multiple of 2^levels), in
+    the Mallat layout: level l replaces the block [:Nx/2^(l-1), :Ny/2^(l-1), :Nz/2^(l-1)]
+    by its one-level transform (low halves first along every axis)."""
+    c = np.asarray(v, np.complex128).copy()
+    n = list(c.shape)
+    for _ in range(levels):
+        blk = c[:n[0], :n[1], :n[2]]
+        for ax in range(3):
+            blk = _haar_axis(blk, ax)
+        c[:n[0], :n[1], :n[2]] = blk
+        n = [m // 2 for m in n]
+    return c
+
+
+def ihaar3(c: np.ndarray, levels: int) -> np.ndarray:
+    """Inverse of haar3."""
+    v = np.asarray(c, np.complex128).copy()
+    shape = v.shape
+    for lev in range(levels - 1, -1, -1):
+        n = [m >> lev for m in shape]
+        blk = v[:n[0], :n[1], :n[2]]
+        for ax in range(3):
+            blk = _ihaar_axis(blk, ax)
+        v[:n[0], :n[1], :n[2]] = blk
+    return v
+
+
+def soft_threshold(c: np.ndarray, tau: float) -> np.ndarray:
+    """Complex soft threshold: c max(1 - tau/|c|, 0) (0 where c = 0)."""
+    mag = np.abs(c)
+    return c * np.where(mag > tau, 1.0 - tau / np.where(mag > 0, mag, 1.0), 0.0)
+
+
+def wavelet_denoise(alpha: np.ndarray, tau: float, levels: int) -> np.ndarray:
+    """Wavelet soft-threshold of the re-joined coefficient volume alpha [Nx][M][K][Ny][Nz]
+    (Nx readout slices): for every (m, k) image, haar3 -> soft-threshold every coefficient
+    outside the coarsest approximation block -> ihaar3."""
+    alpha = np.asarray(alpha, np.complex128)
+    Nx, M, K, Ny, Nz = alpha.shape
+    f = 1 << levels
+    if Nx % f or Ny % f or Nz % f:
+        raise ValueError("every volume size must be a multiple of 2^levels")
+    out = np.empty_like(alpha)
+    for m in range(M):
+        for k in range(K):
+            c = haar3(alpha[:, m, k], levels)
+            keep = c[:Nx // f, :Ny // f, :Nz // f].copy()
+            c = soft_threshold(c, tau)
+            c[:Nx // f, :Ny // f, :Nz // f] = keep
+            out[:, m, k] = ihaar3(c, levels)
+    return out
+
+
+# ----------------------------------------------------------------------------------
 # Pre-processing (Sec. III.A): the acquisition is a sparse array of fully sampled
 # readout lines, line j holding the channels [Ctot][Nx] of phase encode (ky_j, kz_j) at
 # echo t_j.  Index conventions: DC of every axis at index N/2.

@@ -669,3 +669,89 @@ def test_sense_pair_is_adjoint_and_backprojection_round_trips():
     xt = O.backproject(alpha, phi)                     # [M][T][..]
     back = np.einsum("tk,mt...->mk...", phi, xt)       # Phi^T x with orthonormal columns
     assert np.abs(back - alpha).max() < 1e-12 * np.abs(alpha).max()
+
+
+# ----------------------------------------------------------------------------------
+# wavelet soft-threshold of the coefficient volume (Sec. II.C, Sec. III.C)
+# ----------------------------------------------------------------------------------
+def haar_matrix(n):
+    """One level of the orthonormal Haar analysis on n points, written from its
+    definition: row i < n/2 is (e_2i + e_2i+1)/sqrt(2), row n/2 + i is (e_2i - e_2i+1)/sqrt(2)."""
+    H = np.zeros((n, n))
+    for i in range(n // 2):
+        H[i, 2 * i] = H[i, 2 * i + 1] = 1 / np.sqrt(2)
+        H[n // 2 + i, 2 * i] = 1 / np.sqrt(2)
+        H[n // 2 + i, 2 * i + 1] = -1 / np.sqrt(2)
+    return H
+
+
+def dense_pyramid(shape, levels):
+    """Dense matrix of the 3D Haar pyramid on vec(v) (C order): level l is the Kronecker
+    product of the three 1D Haar matrices of the current approximation block, embedded in
+    the identity on every other coefficient."""
+    N = int(np.prod(shape))
+    W = np.eye(N)
+    idx = np.arange(N).reshape(shape)
+    n = list(shape)
+    for _ in range(levels):
+        sub = idx[:n[0], :n[1], :n[2]].ravel()
+        L = np.eye(N)
+        L[np.ix_(sub, sub)] = np.kron(np.kron(haar_matrix(n[0]), haar_matrix(n[1])), haar_matrix(n[2]))
+        W = L @ W
+        n = [m // 2 for m in n]
+    return W
+
+
+@pytest.mark.parametrize("shape,levels", [((4, 2, 4), 1), ((4, 4, 8), 2), ((8, 4, 8), 2), ((8, 8, 8), 3)])
+def test_haar3_is_the_dense_pyramid(shape, levels):
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    W = dense_pyramid(shape, levels)
+    assert np.allclose(W @ W.T, np.eye(W.shape[0]), atol=1e-13)  # orthonormal
+    c = O.haar3(v, levels)
+    assert np.abs(c.ravel() - W @ v.ravel()).max() < 1e-13
+    assert np.abs(O.ihaar3(c, levels) - v).max() < 1e-13
+
+
+def test_wavelet_denoise_threshold_zero_is_identity():
+    rng = np.random.default_rng(12)
+    a = rng.standard_normal((8, 2, 3, 4, 8)) + 1j * rng.standard_normal((8, 2, 3, 4, 8))
+    for lev in (1, 2):
+        assert np.abs(O.wavelet_denoise(a, 0.0, lev) - a).max() < 1e-13
+
+
+def test_wavelet_denoise_large_threshold_is_the_block_mean():
+    """With tau above every detail magnitude only the coarsest Haar approximation is left:
+    the projection on volumes constant over aligned 2^L cubes, i.e. the cube means."""
+    rng = np.random.default_rng(13)
+    a = rng.standard_normal((8, 1, 2, 8, 16)) + 1j * rng.standard_normal((8, 1, 2, 8, 16))
+    for lev in (1, 2, 3):
+        f = 1 << lev
+        got = O.wavelet_denoise(a, 1e6, lev)
+        Nx, M, K, Ny, Nz = a.shape
+        cube = a.reshape(Nx // f, f, M, K, Ny // f, f, Nz // f, f).mean(axis=(1, 5, 7))
+        want = np.repeat(np.repeat(np.repeat(cube, f, axis=0), f, axis=3), f, axis=4)
+        assert np.abs(got - want).max() < 1e-12
+
+
+def test_wavelet_denoise_shrinks_one_detail_atom():
+    """A volume that is one detail basis function times c comes back as
+    max(|c| - tau, 0) e^(i arg c) times the same function; a constant volume is kept."""
+    shape, lev = (4, 4, 8), 2
+    W = dense_pyramid(shape, lev)
+    for i, c in [(5, 3.0 - 4.0j), (100, 0.5j), (127, -2.0)]:  # detail indices (the approximation is 0, 1)
+        atom = (W.T[:, i]).reshape(shape)
+        for tau in (0.1, 1.0, 10.0):
+            got = O.wavelet_denoise((c * atom)[:, None, None], tau, lev)[:, 0, 0]
+            shrink = max(abs(c) - tau, 0.0) / abs(c)
+            assert np.abs(got - shrink * c * atom).max() < 1e-13
+    const = np.full((4, 1, 1, 4, 8), 2.5 - 1j)
+    assert np.abs(O.wavelet_denoise(const, 100.0, lev) - const).max() < 1e-13
+
+
+def test_soft_threshold_closed_form():
+    c = np.array([3 + 4j, -0.3, 0.0, 1j * 2.0])
+    got = O.soft_threshold(c, 1.0)
+    assert np.allclose(np.abs(got), np.maximum(np.abs(c) - 1.0, 0.0), atol=1e-15)
+    nz = np.abs(got) > 0
+    assert np.allclose(got[nz] / np.abs(got[nz]), c[nz] / np.abs(c[nz]))
