@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--cg-iters", type=int, default=3)
     ap.add_argument("--post-te", default="",
                     help="comma-separated echo indices: each step also forms TE images (t2sh_postprocess, pf 0.65)")
+    ap.add_argument("--wavelet", type=int, default=0,
+                    help="levels of the wavelet soft-threshold (t2sh_wavelet_denoise) each step applies to the "
+                         "solved volume; 0: none")
+    ap.add_argument("--wavelet-tau", type=float, default=1e-3)
     ap.add_argument("--preproc", action="store_true",
                     help="time the pre-processing instead (coil compression 16 -> C channels and sparse lines -> "
                          "projected k-space for the whole scan); prints its own JSON line")
@@ -405,6 +409,8 @@ def run_ours(args):
             p.solve_admm(ytil_d, t2sh.KSPACE_PROJ, rho=args.rho, cg_iters=args.cg_iters, out=out_d)
         else:
             p.solve(ytil_d, t2sh.KSPACE_PROJ, out=out_d)
+        if args.wavelet:
+            p.wavelet_denoise(out_d, args.wavelet_tau, args.wavelet)
         if post_te:
             p.postprocess(out_d, post_te, pf=0.65, out=img_d)
         tm = p.timing_read()  # launch counts always; per-class milliseconds only when timing
@@ -502,6 +508,10 @@ def run_ours(args):
     if post_te:  # per echo: alpha and the maps read once, the float image written
         Sx = 1 if args.form == "per-slice" else S
         ab["post"] = len(post_te) * (Sx * sh.nmaps * (sh.nbasis + sh.ncoils) * N * 8 + Sx * N * 4)
+    if args.wavelet:  # read + write of each level's lattice, forward and inverse
+        L = args.wavelet
+        vol = S * sh.nmaps * sh.nbasis * N * 8
+        ab["post"] = ab.get("post", 0) + 2 * vol * (8.0 ** -(L - 1) + 2 * sum(8.0 ** -(l - 1) for l in range(1, L)))
     if args.solver == "admm":
         vec = (1 if args.form == "per-slice" else S) * sh.nmaps * sh.nbasis * N * 8
         ab["llr"] = 4 * vec  # read alpha, u; write v, u
@@ -532,6 +542,7 @@ def run_ours(args):
             "config": {**config_dict(sh, S, iters, world), "precision": args.precision, "form": args.form,
                        **({"solver": f"admm rho={args.rho} cg_iters={args.cg_iters}"} if args.solver == "admm" else {}),
                        **({"post_te": post_te} if post_te else {}), "eig": args.eig,
+                       **({"wavelet": {"levels": args.wavelet, "tau": args.wavelet_tau}} if args.wavelet else {}),
                        **({"col_variant": args.col_variant} if args.col_variant is not None else {})}, "roofline": roof, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": e2e}
     if world == 1 and not args.no_cpu_baseline and args.solver == "fista" and args.form == "batched":

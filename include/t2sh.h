@@ -224,11 +224,26 @@ t2sh_status t2sh_objective(t2sh_plan_t plan, const void* kspace, int32_t kform, 
  *   out = sqrt(sum_c homodyne(x_c(t))^2)           root sum of squares
  * alpha: device [S][M][K][ny][nz] complex64; out: device [S][nte][ny][nz] float32 (caller
  * owned).  1 <= nte <= 8.  Asynchronous on the plan's stream.  Plans made with
- * T2SH_HOST_IO return T2SH_EUNSUPPORTED.  (The paper's 3D wavelet denoising before this
- * step works across readout slices and is not part of it.)
+ * T2SH_HOST_IO return T2SH_EUNSUPPORTED.  (The paper's 3D wavelet denoising that comes
+ * before this step is t2sh_wavelet_denoise.)
  */
 t2sh_status t2sh_postprocess(t2sh_plan_t plan, const void* alpha, const int32_t* te_index, int32_t nte, float pf,
                              void* out);
+
+/*
+ * t2sh_wavelet_denoise -- the wavelet soft-threshold that follows the solve (Sec. II.C
+ * after Eq. 5; the single 3D wavelet soft-thresholding of the re-joined volume in Process
+ * TE, Sec. III.C), in place on alpha: device [S][M][K][ny][nz] complex64, 16-byte
+ * aligned, where the plan's S slices are the whole volume along the readout x.  For every
+ * basis-coefficient image (m, k), the orthonormal 3D Haar pyramid over (x, y, z) with
+ * `levels` levels (each transforms the previous approximation), every detail coefficient
+ * c replaced by c max(1 - tau / |c|, 0), the coarsest approximation kept, then the
+ * inverse pyramid.  The paper names neither the wavelet nor the threshold: the Haar
+ * wavelet and the caller's tau are this library's reading.  Requires 1 <= levels <= 16,
+ * tau finite >= 0, and S, ny, nz multiples of 2^levels (T2SH_EINVAL otherwise).
+ * Asynchronous on the plan's stream; T2SH_HOST_IO plans return T2SH_EUNSUPPORTED.
+ */
+t2sh_status t2sh_wavelet_denoise(t2sh_plan_t plan, void* alpha, float tau, int32_t levels);
 
 /*
  * Pre-processing (Sec. III.A): from the acquisition as a sparse array of fully sampled

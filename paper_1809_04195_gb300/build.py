@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libt2sh.so")
-SOURCES = ["t2sh_api.cu", "k_prep.cu", "k_fft.cu", "k_fft_fast.cu", "k_col_tma.cu", "k_col_tc.cu", "k_col_pr.cu", "k_fused.cu", "k_llr.cu", "k_cg.cu", "k_post.cu", "k_preproc.cu", "t2sh_preproc.cu", "t2sh_noalloc.cu"]
+SOURCES = ["t2sh_api.cu", "k_prep.cu", "k_fft.cu", "k_fft_fast.cu", "k_col_tma.cu", "k_col_tc.cu", "k_col_pr.cu", "k_fused.cu", "k_llr.cu", "k_cg.cu", "k_post.cu", "k_wavelet.cu", "k_preproc.cu", "t2sh_preproc.cu", "t2sh_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

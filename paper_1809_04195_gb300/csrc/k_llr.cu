@@ -29,6 +29,11 @@ struct LlrUnit {
   int s, m0, band, rb;
 };
 
+// Row stride (complex values) of the band in shared memory: nz rounded up to 8 (mod 16),
+// so that rows r and r + 1 start in opposite halves of the 32 banks and the Gram phase's
+// reads of four rows x 8 columns per warp take the minimum two wavefronts.
+__host__ __device__ constexpr int llr_ld(int nz) { return nz + (24 - nz % 16) % 16; }
+
 __device__ __forceinline__ LlrUnit llr_unit(const Geom& g, int b, int unit) {
   const int nbands = (g.ny + b - 1) / b;
   LlrUnit un;
@@ -63,7 +68,7 @@ __device__ __forceinline__ int llr_row0(const Geom& g, const FistaArgs& a, const
   return y >= g.ny ? y - g.ny : y;
 }
 
-// 1. gather the band into gs [K][rb][nz] (gradient step fused for FISTA), threads
+// 1. gather the band into gs [K][rb][llr_ld(nz)] (gradient step fused for FISTA), threads
 // t0 .. t0 + nth - 1 of the CTA
 template <int MODE>
 __device__ __forceinline__ void llr_gather(const Geom& g, const FistaArgs& a, const LlrUnit& un, float2* gs,
@@ -98,7 +103,7 @@ __device__ __forceinline__ void llr_gather(const Geom& g, const FistaArgs& a, co
     } else {
       v = *reinterpret_cast<const float4*>(x + gi);
     }
-    *reinterpret_cast<float4*>(gs + (long long)l * nz + 2 * c.c2) = v;
+    *reinterpret_cast<float4*>(gs + (long long)l * llr_ld(nz) + 2 * c.c2) = v;
     r += c.P;
     while (r >= rb) {
       r -= rb;
@@ -129,7 +134,7 @@ __device__ __forceinline__ void llr_gram(const Geom& g, const FistaArgs& a, cons
     for (int r = r0 < RP ? r0 : rb; r < rb; r += RP) {
       float2 xv[KC];
 #pragma unroll
-      for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[(k * rb + r) * nz + zz] : make_float2(0.f, 0.f);
+      for (int k = 0; k < KC; ++k) xv[k] = (k < K) ? gs[(k * rb + r) * llr_ld(nz) + zz] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < KC; ++k)
 #pragma unroll
@@ -186,7 +191,8 @@ __device__ __forceinline__ void llr_apply(const Geom& g, const FistaArgs& a, con
     float4 xv[KC];  // (pixel zz, pixel zz + 1) of each basis image
 #pragma unroll
     for (int k = 0; k < KC; ++k)
-      xv[k] = (k < K) ? *reinterpret_cast<const float4*>(gs + (k * rb + r) * nz + zz) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[k] = (k < K) ? *reinterpret_cast<const float4*>(gs + (k * rb + r) * llr_ld(nz) + zz)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
     const long long gb = gb0 + (long long)y * nz;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
@@ -244,7 +250,7 @@ __device__ __forceinline__ void llr_res_flush(double* res, float d2, float x2) {
 
 template <int KC>
 __host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
-  return sizeof(float2) * ((size_t)K * b * nz + (size_t)((nz + b - 1) / b) * KC * KC) +
+  return sizeof(float2) * ((size_t)K * b * llr_ld(nz) + (size_t)((nz + b - 1) / b) * KC * KC) +
          sizeof(float) * (size_t)((nz + b - 1) / b) * KC * KC;
 }
 
@@ -263,8 +269,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
   const int nbands = (g.ny + a.b - 1) / a.b;
   const LlrUnit un = llr_unit(g, a.b, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x);
   const int nbz = (g.nz + a.b - 1) / a.b;
-  float2* gs = smem;                                         // [K][rb][nz]
-  float2* wm = gs + (size_t)g.K * un.rb * g.nz;              // [nbz][KC][KC]
+  float2* gs = smem;                                         // [K][rb][llr_ld(nz)]
+  float2* wm = gs + (size_t)g.K * un.rb * llr_ld(g.nz);      // [nbz][KC][KC]
   float* gram = reinterpret_cast<float*>(wm + (size_t)nbz * KC * KC);  // [nbz][KC*KC]
   llr_gather<MODE>(g, a, un, gs, x, z, grad, aty, u, 0, kThreads);
   __syncthreads();

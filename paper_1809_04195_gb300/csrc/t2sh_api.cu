@@ -940,6 +940,24 @@ t2sh_status t2sh_postprocess(t2sh_plan_t p, const void* alpha, const int32_t* te
   return T2SH_OK;
 }
 
+t2sh_status t2sh_wavelet_denoise(t2sh_plan_t p, void* alpha, float tau, int32_t levels) {
+  T2SH_REQ(p && alpha, "NULL argument");
+  const t2sh_dims& d = p->d;
+  if (p->host_io) {
+    set_err("t2sh_wavelet_denoise takes device pointers (the plan has T2SH_HOST_IO)");
+    return T2SH_EUNSUPPORTED;
+  }
+  T2SH_REQ(((uintptr_t)alpha & 15) == 0, "alpha must be 16-byte aligned");
+  T2SH_REQ(levels >= 1 && levels <= 16, "levels must be in [1, 16]");
+  T2SH_REQ(std::isfinite(tau) && tau >= 0.f, "tau must be finite and >= 0");
+  const int f = 1 << levels;
+  T2SH_REQ(d.nslices % f == 0 && d.ny % f == 0 && d.nz % f == 0,
+           "nslices = %d, ny = %d and nz = %d must be multiples of 2^levels = %d", d.nslices, d.ny, d.nz, f);
+  KTimer k(p, KC_POST);
+  T2SH_CK(launch_wavelet_denoise(p->g, static_cast<float2*>(alpha), tau, levels, p->st));
+  return T2SH_OK;
+}
+
 t2sh_status t2sh_solve_begin(t2sh_plan_t p, const void* kspace, int32_t kform) {
   return begin_impl(p, kspace, kform, true);
 }

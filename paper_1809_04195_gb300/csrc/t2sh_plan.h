@@ -146,6 +146,10 @@ cudaError_t smem_optin(const void* kernel, int bytes);
 cudaError_t sm_count(int* n);
 cudaError_t ctas_per_sm(const void* kernel, int threads, size_t smem, int* per);
 
+// wavelet soft-threshold of the coefficient volume alpha [S][M][K][ny][nz] in place (k_wavelet.cu):
+// `levels`-level orthonormal 3D Haar pyramid over (slice, y, z), details soft-thresholded by tau
+cudaError_t launch_wavelet_denoise(const Geom& g, float2* alpha, float tau, int levels, cudaStream_t st);
+
 int row_rows_per_cta(const Geom& g);
 int col_cols_per_cta(const Geom& g);
 

@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "t2sh_solve_admm": [_vp, _vp, _i32, _vp, _f32, _i32, ctypes.POINTER(ctypes.c_double)],
             "t2sh_objective": [_vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_double)],
             "t2sh_postprocess": [_vp, _vp, ctypes.POINTER(_i32), _i32, _f32, _vp],
+            "t2sh_wavelet_denoise": [_vp, _vp, _f32, _i32],
             "t2sh_coil_compression": [ctypes.POINTER(Sparse), _vp, _i32, _i32, _vp, _vp],
             "t2sh_preprocess": [ctypes.POINTER(Sparse), _vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp],
             "t2sh_get_step": [_vp, ctypes.POINTER(_f32)],
@@ -392,6 +393,14 @@ class Plan:
         tarr = (_i32 * len(te))(*te)
         _check(lib().t2sh_postprocess(self._h, ap, tarr, len(te), float(pf), op))
         return out
+
+    def wavelet_denoise(self, alpha, tau: float, levels: int = 1):
+        """In place on alpha [S][M][K][ny][nz] (device): orthonormal 3D Haar pyramid over
+        (slice, y, z) with `levels` levels, details soft-thresholded by tau, inverse."""
+        import torch
+        ap = _ptr(alpha, torch.complex64, self.vec_shape, False)
+        _check(lib().t2sh_wavelet_denoise(self._h, ap, float(tau), int(levels)))
+        return alpha
 
     # -- resumable solve (schedulers interleaving scans) --------------------------------
     def solve_begin(self, kspace, kform=KSPACE_PROJ):
