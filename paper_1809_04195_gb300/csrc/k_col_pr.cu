@@ -12,6 +12,8 @@
 // R1 odd (the stage-A exchange stride), K <= 4, nz % W == 0.
 #include <algorithm>
 
+// packed two-lane complex additions in the butterflies: measured 2.6 % faster here
+#define T2SH_PACKED_ADD 1
 #include "t2sh_device.cuh"
 
 namespace t2sh {

@@ -11,11 +11,28 @@
 
 namespace t2sh {
 
+// A translation unit that defines T2SH_PACKED_ADD before including this header gets the
+// complex additions and subtractions of every butterfly as packed two-lane float32
+// instructions (one instruction per complex value).  The arithmetic is the same per
+// component; whether it pays depends on the kernel (measured faster for the row passes,
+// slower for the TMA column pass), so it is chosen per translation unit.  The two forms
+// live in different inline namespaces, so their definitions never collide.
+#if defined(T2SH_PACKED_ADD)
+inline namespace packed_add {
+#else
+inline namespace scalar_add {
+#endif
+
 // ---------------------------------------------------------------------------------
 // complex float helpers (interleaved float2)
 // ---------------------------------------------------------------------------------
+#if defined(T2SH_PACKED_ADD)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+#else
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -434,6 +451,128 @@ __device__ __forceinline__ void herm_jacobi(T (&ar)[K][K], T (&ai)[K][K], T (&vr
   }
 }
 
+// Round-robin (tournament) ordering of the K (K - 1) / 2 index pairs of an even K into
+// K - 1 rounds of K / 2 disjoint pairs: in round r, i < K - 1 meets j = (r - i) mod (K - 1),
+// and the i with j = i meets K - 1.
+__host__ __device__ constexpr int jac_pair(int K, int r, int m, bool second) {
+  int cnt = 0;
+  for (int i = 0; i < K - 1; ++i) {
+    const int j = ((r - i) % (K - 1) + (K - 1)) % (K - 1);
+    int a = i, b = j;
+    if (i == j) b = K - 1;
+    else if (i > j) continue;
+    if (cnt == m) return second ? b : a;
+    ++cnt;
+  }
+  return 0;
+}
+
+// The same Jacobi method with each sweep taken as K - 1 rounds of K / 2 disjoint pivots
+// (the parallel ordering): a round's rotations act on disjoint rows and columns, so they
+// commute and their parameters all come from the matrix before the round.  One thread
+// then works on K / 2 independent rotations at a time instead of one dependent chain.
+// Same interface and stopping rule as herm_jacobi; K even.
+template <typename T, int K>
+__device__ __forceinline__ void herm_jacobi_rounds(T (&ar)[K][K], T (&ai)[K][K], T (&vr)[K][K], T (&vi)[K][K],
+                                                   int max_sweeps) {
+  static_assert(K % 2 == 0, "the round-robin ordering needs an even size");
+  constexpr int H = K / 2;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      vr[i][j] = (i == j) ? T(1) : T(0);
+      vi[i][j] = T(0);
+    }
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = 0, diag = 0;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      diag += ar[p][p] * ar[p][p];
+#pragma unroll
+      for (int q = p + 1; q < K; ++q) off += ar[p][q] * ar[p][q] + ai[p][q] * ai[p][q];
+    }
+    if (!(off > JacobiTol<T>::rel2 * diag)) break;
+#pragma unroll
+    for (int rd = 0; rd < K - 1; ++rd) {
+      // parameters of the round's rotations, all from the matrix before the round
+      T dr[H], di[H], rr[H], tt[H], cc[H], ss[H];
+      bool on[H];
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const int p = jac_pair(K, rd, m, false), q = jac_pair(K, rd, m, true);
+        const T xr = ar[p][q], xi = ai[p][q];
+        const T r2 = xr * xr + xi * xi;
+        on[m] = r2 > JacobiTol<T>::pivot2;
+        const T ir = on[m] ? jac_rsqrt(r2) : T(0);
+        rr[m] = r2 * ir;
+        dr[m] = on[m] ? xr * ir : T(1);  // phase d = conj(a_pq) / |a_pq|
+        di[m] = -xi * ir;
+        const T theta = (ar[q][q] - ar[p][p]) * (T(0.5) * ir);
+        const T at = fabs(theta);
+        T t;
+        if (at > T(1e18)) {
+          t = T(0.5) / at;
+        } else {
+          const T u = at * at + T(1);
+          t = jac_rcp(at + u * jac_rsqrt(u));
+        }
+        if (theta < T(0)) t = -t;
+        if (!on[m]) t = T(0);
+        tt[m] = t;
+        cc[m] = jac_rsqrt(t * t + T(1));
+        ss[m] = t * cc[m];
+      }
+      // phases: column q *= d, row q *= conj(d); V column q *= d
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const int q = jac_pair(K, rd, m, true);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (k != q) {
+            const T yr = ar[k][q] * dr[m] - ai[k][q] * di[m];
+            const T yi = ar[k][q] * di[m] + ai[k][q] * dr[m];
+            ar[k][q] = yr; ai[k][q] = yi;
+            ar[q][k] = yr; ai[q][k] = -yi;
+          }
+          const T wr = vr[k][q] * dr[m] - vi[k][q] * di[m];
+          const T wi = vr[k][q] * di[m] + vi[k][q] * dr[m];
+          vr[k][q] = wr; vi[k][q] = wi;
+        }
+      }
+      // real rotations on the now real pivots
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const int p = jac_pair(K, rd, m, false), q = jac_pair(K, rd, m, true);
+        const T c = cc[m], sn = ss[m];
+        ar[p][p] -= tt[m] * rr[m];
+        ar[q][q] += tt[m] * rr[m];
+        ar[p][q] = T(0); ar[q][p] = T(0);
+        ai[p][q] = T(0); ai[q][p] = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (k != p && k != q) {
+            const T akp_r = ar[k][p], akp_i = ai[k][p];
+            const T akq_r = ar[k][q], akq_i = ai[k][q];
+            const T nkp_r = c * akp_r - sn * akq_r, nkp_i = c * akp_i - sn * akq_i;
+            const T nkq_r = sn * akp_r + c * akq_r, nkq_i = sn * akp_i + c * akq_i;
+            ar[k][p] = nkp_r; ai[k][p] = nkp_i; ar[p][k] = nkp_r; ai[p][k] = -nkp_i;
+            ar[k][q] = nkq_r; ai[k][q] = nkq_i; ar[q][k] = nkq_r; ai[q][k] = -nkq_i;
+          }
+          const T vkp_r = vr[k][p], vkp_i = vi[k][p];
+          const T vkq_r = vr[k][q], vkq_i = vi[k][q];
+          vr[k][p] = c * vkp_r - sn * vkq_r; vi[k][p] = c * vkp_i - sn * vkq_i;
+          vr[k][q] = sn * vkp_r + c * vkq_r; vi[k][q] = sn * vkp_i + c * vkq_i;
+        }
+      }
+    }
+  }
+}
+static_assert(jac_pair(4, 0, 0, false) == 0 && jac_pair(4, 0, 0, true) == 3 && jac_pair(4, 0, 1, false) == 1 &&
+                  jac_pair(4, 0, 1, true) == 2 && jac_pair(4, 1, 0, true) == 1 && jac_pair(4, 1, 1, false) == 2 &&
+                  jac_pair(4, 2, 0, true) == 2 && jac_pair(4, 2, 1, true) == 3,
+              "round-robin pairs of 4");
+
 // ---------------------------------------------------------------------------------
 // Asynchronous global -> shared copies (cp.async, completion per commit group).
 // ---------------------------------------------------------------------------------
@@ -469,8 +608,8 @@ __device__ __forceinline__ void svt_weights(const float* gp, float tau, float2* 
       else if (k < l) { ar[k][l] = gp[k * KC + l]; ai[k][l] = gp[l * KC + k]; }
       else { ar[k][l] = gp[l * KC + k]; ai[k][l] = -gp[k * KC + l]; }
     }
-  // Five cyclic sweeps converge a 4 x 4 Hermitian matrix to working precision.
-  herm_jacobi<ET, KC>(ar, ai, vr, vi, 5);
+  // Five sweeps converge a 4 x 4 Hermitian matrix to working precision.
+  herm_jacobi_rounds<ET, KC>(ar, ai, vr, vi, 5);
   // Rotations accumulated in float32 drift V away from orthonormal, and FISTA's
   // momentum amplifies the resulting error in W; so re-orthonormalise V (modified
   // Gram-Schmidt) and take each eigenvalue as the Rayleigh quotient v^H G v on the
@@ -683,4 +822,5 @@ __device__ __forceinline__ void split_bf16(float2 v, unsigned& hi, unsigned& lo)
 // sign (-1)^(a) as float
 __device__ __forceinline__ float parity_sign(int a) { return (a & 1) ? -1.0f : 1.0f; }
 
+}  // inline namespace
 }  // namespace t2sh
