@@ -34,6 +34,12 @@ struct LlrUnit {
 // reads of four rows x 8 columns per warp take the minimum two wavefronts.
 __host__ __device__ constexpr int llr_ld(int nz) { return nz + (24 - nz % 16) % 16; }
 
+// Per-block strides of the Gram matrices (floats) and threshold weights (complex): one
+// more than KC * KC, so that the blocks a warp touches at once (the eigen-step threads,
+// and the eight blocks under a warp's 64 pixels in the apply step) fall in different banks.
+template <int KC> constexpr int kGramStride = KC * KC + 1;
+template <int KC> constexpr int kWStride = KC * KC + 1;
+
 __device__ __forceinline__ LlrUnit llr_unit(const Geom& g, int b, int unit) {
   const int nbands = (g.ny + b - 1) / b;
   LlrUnit un;
@@ -154,7 +160,7 @@ __device__ __forceinline__ void llr_gram(const Geom& g, const FistaArgs& a, cons
 #pragma unroll
       for (int k = 0; k < KC; ++k)
 #pragma unroll
-        for (int l = 0; l < KC; ++l) gram[blk * KC * KC + k * KC + l] = gr[k][l];
+        for (int l = 0; l < KC; ++l) gram[blk * kGramStride<KC> + k * KC + l] = gr[k][l];
     }
   }
 }
@@ -163,7 +169,7 @@ __device__ __forceinline__ void llr_gram(const Geom& g, const FistaArgs& a, cons
 template <int KC, typename ET>
 __device__ __forceinline__ void llr_eigen(const float* gram, float tau, float2* wm, int nblk, int t0, int nth) {
   for (int blk = (int)threadIdx.x - t0; blk < nblk; blk += nth)
-    svt_weights<ET, KC>(gram + blk * KC * KC, tau, wm + (size_t)blk * KC * KC);
+    svt_weights<ET, KC>(gram + blk * kGramStride<KC>, tau, wm + (size_t)blk * kWStride<KC>);
 }
 
 // 4. X' = X W, then the FISTA momentum or the ADMM dual; write back.  The optional
@@ -181,8 +187,8 @@ __device__ __forceinline__ void llr_apply(const Geom& g, const FistaArgs& a, con
   int d0 = zz - a.sz % nz;
   d0 += d0 < 0 ? nz : 0;
   const int d1 = d0 + 1 == nz ? 0 : d0 + 1;
-  const float2* w0 = wm + (size_t)(d0 / b) * KC * KC;
-  const float2* w1 = wm + (size_t)(d1 / b) * KC * KC;
+  const float2* w0 = wm + (size_t)(d0 / b) * kWStride<KC>;
+  const float2* w1 = wm + (size_t)(d1 / b) * kWStride<KC>;
   const int y0 = llr_row0(g, a, un);
   const long long gb0 = ((long long)(un.s * g.M + un.m0) * K) * N + zz;
   for (int r = c.lp; r < rb; r += c.P) {
@@ -250,8 +256,8 @@ __device__ __forceinline__ void llr_res_flush(double* res, float d2, float x2) {
 
 template <int KC>
 __host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
-  return sizeof(float2) * ((size_t)K * b * llr_ld(nz) + (size_t)((nz + b - 1) / b) * KC * KC) +
-         sizeof(float) * (size_t)((nz + b - 1) / b) * KC * KC;
+  return sizeof(float2) * ((size_t)K * b * llr_ld(nz) + (size_t)((nz + b - 1) / b) * kWStride<KC>) +
+         sizeof(float) * (size_t)((nz + b - 1) / b) * kGramStride<KC>;
 }
 
 // The K <= 4 float32 variant is held to 80 registers (three CTAs per SM) or, where four
@@ -270,8 +276,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
   const LlrUnit un = llr_unit(g, a.b, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x);
   const int nbz = (g.nz + a.b - 1) / a.b;
   float2* gs = smem;                                         // [K][rb][llr_ld(nz)]
-  float2* wm = gs + (size_t)g.K * un.rb * llr_ld(g.nz);      // [nbz][KC][KC]
-  float* gram = reinterpret_cast<float*>(wm + (size_t)nbz * KC * KC);  // [nbz][KC*KC]
+  float2* wm = gs + (size_t)g.K * un.rb * llr_ld(g.nz);      // [nbz][kWStride]: KC x KC weights
+  float* gram = reinterpret_cast<float*>(wm + (size_t)nbz * kWStride<KC>);  // [nbz][kGramStride]
   llr_gather<MODE>(g, a, un, gs, x, z, grad, aty, u, 0, kThreads);
   __syncthreads();
   llr_gram<KC>(g, a, un, gs, gram, 0, kThreads / 32);
