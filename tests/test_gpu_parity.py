@@ -139,6 +139,25 @@ def test_step_matches_oracle(T):
     assert abs(mu - 1.0 / L) <= 1e-5 / L
 
 
+def test_plan_step_is_shared_by_its_slices(T):
+    """A plan's slices share one step, 1/L with L the largest Lipschitz bound over its slices
+    (a valid step for each of them).  With coil maps of a different scale in every slice the
+    library takes that smallest step, and the oracle's FISTA given the same step agrees
+    slice by slice."""
+    rng, phi, mask, maps = random_problem(14, 3, 48, 40, 3, 16, 4, 1, frac=0.3)
+    (maps,) = r32(maps=maps * np.array([1.0, 0.6, 1.5])[:, None, None, None, None])
+    y = crandn(rng, 3, 3, 16, 48, 40) * mask[None, None] * 0.1
+    ys = y.astype(np.complex64).astype(np.complex128)
+    psi = O.space_time_kernel(mask, phi)
+    L = max(O.lipschitz(maps[s], psi) for s in range(3))
+    with make_plan(T, phi, mask, maps, block=8, lam=0.02, iters=15, seed=3) as p:
+        assert abs(p.step - 1.0 / L) <= 1e-5 / L
+        got = host(p.solve(c64(y), T.KSPACE_TE))
+    for s in range(3):
+        ref = O.fista(ys[s], "te", maps[s], mask, phi, 0.02, 8, 15, 3, step=1.0 / L)
+        assert nrmse(got[s], ref) < SOLVE_TOL
+
+
 @pytest.mark.parametrize("ny,nz,b,sy,sz,M,K", [
     (64, 48, 8, 3, 5, 1, 4),
     (60, 36, 8, 7, 2, 1, 4),    # partial blocks on both axes
