@@ -66,6 +66,8 @@ def parse():
                          "batch3: three scans of different shapes in one batched solve (t2sh_solve_batch)")
     ap.add_argument("--eig", choices=["fp32", "fp64"], default="fp32",
                     help="precision of the LLR K x K eigendecomposition (fp64: T2SH_EIG_FP64)")
+    ap.add_argument("--batch-schedule", choices=["list", "per-scan"], default="list",
+                    help="batch3: one LLR launch per iteration over all scans (list) or one per scan")
     ap.add_argument("--prof-steps", type=int, default=2,
                     help="steps of the separate instrumented pass that gives the per-kernel times")
     return ap.parse_args()
@@ -574,6 +576,7 @@ def run_batch3(args):
     dev = torch.device("cuda", 0)
     prec = t2sh.MIXED_BF16 if args.precision == "mixed" else t2sh.FP32
     eflags = t2sh.EIG_FP64 if args.eig == "fp64" else 0
+    t2sh.batch_schedule(args.batch_schedule == "per-scan")
     scans = []
     for sh in synth.BATCH_SCANS:
         S = args.slices or sh.nslices
@@ -624,7 +627,8 @@ def run_batch3(args):
             "vs_baseline": None,
             "dtype": "f32" if prec == t2sh.FP32 else "f32 + bf16x3 (column DFTs on tensor cores, f32 accumulate)",
             "data": "synthetic (seeded 3D ellipsoid phantoms, smooth coil maps, variable-density masks)",
-            "config": {**batch3_config(1), "precision": args.precision, "eig": args.eig},
+            "config": {**batch3_config(1), "precision": args.precision, "eig": args.eig,
+                       "batch_schedule": args.batch_schedule},
             "roofline": {"bound": "hbm", "kernel": "whole batched solve (all kernels, plans included)",
                          "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "peak_source": src, "traffic": None,

@@ -306,14 +306,26 @@ t2sh_status t2sh_solve_end(t2sh_plan_t plan, void* alpha_out, double* residual_o
 
 /*
  * t2sh_solve_batch -- solve n plans at once (scans of different sizes and coil counts:
- * the batched multi-scan form).  Each plan runs on a stream forked from `stream`; all
- * iterations of all plans are captured into one CUDA graph, which is launched once, so
- * the scans' kernels overlap on the GPU.  kspace[i] / kform[i] / alpha_out[i] as for
- * t2sh_solve (device pointers; plans with T2SH_HOST_IO are rejected).  A plan may
- * appear once.  Synchronous: returns when every alpha_out is written.
+ * the batched multi-scan form, the paper's many slices per machine of Sec. IV.E).  Each
+ * plan's normal operator runs on a stream forked from `stream`; all iterations of all
+ * plans are captured into one CUDA graph, which is launched once, so the scans' kernels
+ * overlap on the GPU.  The LLR step of each iteration is one launch over a work list of
+ * (scan, slice, map set, band) units of every plan still iterating, when the plans share
+ * the LLR variant (all K <= 4 or all K > 4, the same T2SH_EIG_FP64) and none uses
+ * T2SH_FUSED_ROWS; otherwise each plan launches its own on its stream.  kspace[i] /
+ * kform[i] / alpha_out[i] as for t2sh_solve (device pointers; plans with T2SH_HOST_IO are
+ * rejected).  A plan may appear once.  Synchronous: returns when every alpha_out is
+ * written.  Results equal the plans' single solves bit for bit.
  */
 t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* kspace, const int32_t* kform,
                              void* const* alpha_out, void* stream);
+
+/*
+ * t2sh_batch_schedule -- process-wide choice for t2sh_solve_batch: 0 (default) the LLR
+ * work list described there, 1 one LLR launch per plan on its own stream (for
+ * comparison).  Affects solves that start after the call.  The paper has no counterpart.
+ */
+t2sh_status t2sh_batch_schedule(int32_t per_scan_llr);
 
 /*
  * t2sh_autotune -- choose, for the plan's problem shape, the column-pass variant

@@ -267,13 +267,12 @@ __host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
 // MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
 // z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
 // u <- w - v.
-template <int KC, int MODE, typename ET, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
-    k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
-          const float2* __restrict__ aty, float2* u) {
+// One CTA's work: unit = (slice s, map set m0, band) decoded by llr_unit.
+template <int KC, int MODE, typename ET>
+__device__ __forceinline__ void llr_band(const Geom& g, const FistaArgs& a, int unit, float2* x, float2* z,
+                                         const float2* __restrict__ grad, const float2* __restrict__ aty, float2* u) {
   extern __shared__ float2 smem[];
-  const int nbands = (g.ny + a.b - 1) / a.b;
-  const LlrUnit un = llr_unit(g, a.b, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x);
+  const LlrUnit un = llr_unit(g, a.b, unit);
   const int nbz = (g.nz + a.b - 1) / a.b;
   float2* gs = smem;                                         // [K][rb][llr_ld(nz)]
   float2* wm = gs + (size_t)g.K * un.rb * llr_ld(g.nz);      // [nbz][kWStride]: KC x KC weights
@@ -288,6 +287,26 @@ __global__ void __launch_bounds__(kThreads, MINB)
   float d2 = 0.f, x2 = 0.f;
   llr_apply<KC, MODE>(g, a, un, gs, wm, x, z, u, want_res, d2, x2);
   if (want_res) llr_res_flush(a.res, d2, x2);
+}
+
+template <int KC, int MODE, typename ET, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+    k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
+          const float2* __restrict__ aty, float2* u) {
+  const int nbands = (g.ny + a.b - 1) / a.b;
+  llr_band<KC, MODE, ET>(g, a, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x, x, z, grad, aty, u);
+}
+
+// Work-list form for batched solves: one launch runs the FISTA LLR step of several scans;
+// CTA i belongs to the last job whose first unit is <= i (jobs in increasing unit0).
+template <int KC, typename ET, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_llr_list(const LlrJob* __restrict__ jobs, int njobs) {
+  int j = 0;
+  while (j + 1 < njobs && jobs[j + 1].unit0 <= (int)blockIdx.x) ++j;
+  const Geom g = jobs[j].g;
+  const FistaArgs a = jobs[j].a;
+  llr_band<KC, LLR_FISTA, ET>(g, a, (int)blockIdx.x - jobs[j].unit0, jobs[j].x, jobs[j].z, jobs[j].grad,
+                              jobs[j].aty, nullptr);
 }
 
 template <int KC, int MODE, typename ET, int MINB>
@@ -336,6 +355,25 @@ cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, 
 cudaError_t launch_llr_admm(const Geom& g, const FistaArgs& a, const float2* alpha, float2* v, float2* u,
                             cudaStream_t st) {
   return llr_mode<LLR_ADMM>(g, a, const_cast<float2*>(alpha), v, nullptr, nullptr, u, st);
+}
+
+int llr_units(const Geom& g, int b) { return ((g.ny + b - 1) / b) * g.S * g.M; }
+
+cudaError_t launch_llr_list(const LlrJob* jobs, int njobs, int units, bool kc8, bool eig64, size_t smem,
+                            cudaStream_t st) {
+  if (njobs <= 0 || units <= 0) return cudaSuccess;
+  auto go = [&](auto kern, int minb_unused) -> cudaError_t {
+    (void)minb_unused;
+    const cudaError_t e = smem_optin((const void*)kern, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    kern<<<units, kThreads, smem, st>>>(jobs, njobs);
+    return cudaGetLastError();
+  };
+  // the same register bounds as the per-scan launches (llr_go)
+  if (eig64) return kc8 ? go(k_llr_list<8, double, 1>, 1) : go(k_llr_list<4, double, 1>, 1);
+  if (kc8) return go(k_llr_list<8, float, 1>, 1);
+  if (4 * (smem + 1024) <= 228 * 1024) return go(k_llr_list<4, float, 4>, 4);
+  return go(k_llr_list<4, float, 3>, 3);
 }
 
 size_t llr_smem_bytes(const Geom& g, int b) {

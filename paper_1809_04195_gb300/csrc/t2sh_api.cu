@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <atomic>
 #include <tuple>
 #include <vector>
 
@@ -674,16 +675,14 @@ t2sh_status begin_impl(t2sh_plan_t p, const void* kspace, int32_t kform, bool re
   return T2SH_OK;
 }
 
-// One FISTA iteration (index p->iter_done) of Eq. 5.
-t2sh_status iteration(t2sh_plan_t p) {
+// FISTA arguments of iteration `it` of plan p when t_k = tk before it; *tn gets t_{k+1}.
+FistaArgs fista_args(t2sh_plan_t p, int it, double tk, double* tn) {
   const t2sh_dims& d = p->d;
-  const size_t vec = cbytes((long long)p->g.S * p->g.M * p->g.K * p->g.ny * p->g.nz);  // slices in view
-  const int it = p->iter_done;
-  const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * p->tk * p->tk));
+  *tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * tk * tk));
   FistaArgs a{};
   a.mu = p->mu;
   a.tau = p->mu * d.lambda;
-  a.beta = (float)((p->tk - 1.0) / tn);
+  a.beta = (float)((tk - 1.0) / *tn);
   a.sy = p->shifts[2 * it];
   a.sz = p->shifts[2 * it + 1];
   a.b = d.block;
@@ -691,6 +690,16 @@ t2sh_status iteration(t2sh_plan_t p) {
   a.skip_adj = (it == 0);
   a.skip_fwd = (it == d.iters - 1);
   a.res = p->record_res ? p->res + 2 * it : nullptr;
+  return a;
+}
+
+// One FISTA iteration (index p->iter_done) of Eq. 5.
+t2sh_status iteration(t2sh_plan_t p) {
+  const t2sh_dims& d = p->d;
+  const size_t vec = cbytes((long long)p->g.S * p->g.M * p->g.K * p->g.ny * p->g.nz);  // slices in view
+  const int it = p->iter_done;
+  double tn = 0.0;
+  const FistaArgs a = fista_args(p, it, p->tk, &tn);
   if (p->fused_rows && band_fused_supported(p->g, d.block)) {
     // column pass of the normal operator, then the band kernel: A^H A z, gradient,
     // LLR, momentum and DFT_z(S z_{k+1}) for the next iteration (z_0 = 0: no A^H A z_0)
@@ -722,6 +731,102 @@ t2sh_status iterate_impl(t2sh_plan_t p, int n) {
   for (int i = 0; i < n && p->iter_done < p->d.iters; ++i) {
     t2sh_status s = iteration(p);
     if (s != T2SH_OK) return s;
+  }
+  return T2SH_OK;
+}
+
+// 0: batched solves launch the LLR step of all scans as one work list when they qualify;
+// 1: one LLR launch per scan on the scan's own stream (t2sh_batch_schedule)
+std::atomic<int> g_batch_per_scan_llr{0};
+
+// The FISTA iterations of several begun plans as one work list per stage: every iteration
+// runs each active plan's normal operator on that plan's stream (plans[i]->st), then one
+// LLR launch on `origin` covers the bands of every active plan, from a per-iteration job
+// table prepared in device memory before the caller begins stream capture.  Only for
+// plans that all take the FISTA LLR of the same register variant (K <= 4 or not, float32
+// or float64 eigen-step) and no fused row kernel; see batch_list_eligible.
+struct BatchList {
+  std::vector<LlrJob> jobs;      // all iterations, in order
+  std::vector<int> off, count;   // per iteration: first job, number of jobs
+  std::vector<int> units;        // per iteration: CTAs
+  std::vector<double> tk_end;    // per plan: t_k after its last iteration
+  size_t smem = 0;
+  bool kc8 = false, eig64 = false;
+  LlrJob* dev = nullptr;
+};
+
+bool batch_list_eligible(t2sh_plan_t* plans, int n) {
+  for (int i = 0; i < n; ++i) {
+    const t2sh_plan_t p = plans[i];
+    if (p->fused_rows && band_fused_supported(p->g, p->d.block)) return false;
+    if ((p->g.K > 4) != (plans[0]->g.K > 4)) return false;
+    if (((p->d.flags ^ plans[0]->d.flags) & T2SH_EIG_FP64) != 0) return false;
+  }
+  return true;
+}
+
+void batch_list_prepare(t2sh_plan_t* plans, int n, BatchList& bl) {
+  int maxit = 0;
+  for (int i = 0; i < n; ++i) maxit = std::max(maxit, plans[i]->d.iters);
+  std::vector<double> tk(n);
+  for (int i = 0; i < n; ++i) tk[i] = plans[i]->tk;
+  bl.kc8 = plans[0]->g.K > 4;
+  bl.eig64 = (plans[0]->d.flags & T2SH_EIG_FP64) != 0;
+  for (int it = 0; it < maxit; ++it) {
+    bl.off.push_back((int)bl.jobs.size());
+    int units = 0;
+    for (int i = 0; i < n; ++i) {
+      const t2sh_plan_t p = plans[i];
+      if (it >= p->d.iters) continue;
+      double tn = 0.0;
+      LlrJob j{};
+      j.g = p->g;
+      j.a = fista_args(p, it, tk[i], &tn);
+      j.x = p->x;
+      j.z = p->z;
+      j.grad = p->grad;
+      j.aty = p->aty;
+      j.unit0 = units;
+      units += llr_units(p->g, p->d.block);
+      bl.smem = std::max(bl.smem, llr_smem_bytes(p->g, p->d.block));
+      bl.jobs.push_back(j);
+      tk[i] = tn;
+    }
+    bl.count.push_back((int)bl.jobs.size() - bl.off.back());
+    bl.units.push_back(units);
+  }
+  bl.tk_end = tk;
+}
+
+// Enqueue (for capture) every iteration of the work-list batch.
+t2sh_status batch_list_iterate(t2sh_plan_t* plans, int n, const BatchList& bl, cudaStream_t origin,
+                               std::vector<cudaEvent_t>& ev) {
+  const int maxit = (int)bl.off.size();
+  for (int it = 0; it < maxit; ++it) {
+    T2SH_CK(cudaEventRecord(ev[n + 1], origin));
+    for (int i = 0; i < n; ++i) {
+      const t2sh_plan_t p = plans[i];
+      if (it >= p->d.iters) continue;
+      T2SH_CK(cudaStreamWaitEvent(p->st, ev[n + 1], 0));
+      if (it == 0) {
+        T2SH_CK(cudaMemsetAsync(p->grad, 0, footprint(p->d).vec, p->st));  // z_0 = 0
+      } else {
+        const t2sh_status s = normal_op(p, p->z, p->grad);
+        if (s != T2SH_OK) return s;
+      }
+      T2SH_CK(cudaEventRecord(ev[i], p->st));
+      T2SH_CK(cudaStreamWaitEvent(origin, ev[i], 0));
+    }
+    for (int i = 0; i < n; ++i)
+      if (it < plans[i]->d.iters) {
+        plans[i]->launches[KC_LLR]++;  // one launch, counted once
+        break;
+      }
+    T2SH_CK(launch_llr_list(bl.dev + bl.off[it], bl.count[it], bl.units[it], bl.kc8, bl.eig64, bl.smem, origin));
+  }
+  for (int i = 0; i < n; ++i) {
+    plans[i]->tk = bl.tk_end[i];
+    plans[i]->iter_done = plans[i]->d.iters;
   }
   return T2SH_OK;
 }
@@ -993,6 +1098,8 @@ t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* k
   cudaGraphExec_t exec = nullptr;
   t2sh_status st = T2SH_OK;
   cudaStream_t origin = nullptr;
+  BatchList bl;
+  const bool use_list = batch_list_eligible(plans, n) && !g_batch_per_scan_llr;
 #define B_CK(call)                                                                   \
   do {                                                                               \
     cudaError_t e_ = (call);                                                         \
@@ -1018,18 +1125,33 @@ t2sh_status t2sh_solve_batch(t2sh_plan_t* plans, int32_t n, const void* const* k
     B_CK(cudaEventRecord(ev[i], fs[i]));
     B_CK(cudaStreamWaitEvent(origin, ev[i], 0));
   }
+  if (use_list) {  // the per-iteration LLR job tables, in device memory before the capture
+    batch_list_prepare(plans, n, bl);
+    if (!bl.jobs.empty()) {
+      B_CK(cudaMalloc(&bl.dev, sizeof(LlrJob) * bl.jobs.size()));
+      B_CK(cudaMemcpy(bl.dev, bl.jobs.data(), sizeof(LlrJob) * bl.jobs.size(), cudaMemcpyHostToDevice));
+    }
+  }
   // capture all iterations of all plans
   B_CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed));
-  B_CK(cudaEventRecord(ev[n + 1], origin));
-  for (int i = 0; i < n; ++i) {
-    B_CK(cudaStreamWaitEvent(fs[i], ev[n + 1], 0));
-    st = iterate_impl(plans[i], plans[i]->d.iters);
+  if (use_list) {
+    st = batch_list_iterate(plans, n, bl, origin, ev);
     if (st != T2SH_OK) {
       cudaStreamEndCapture(origin, &graph);
       goto done;
     }
-    B_CK(cudaEventRecord(ev[i], fs[i]));
-    B_CK(cudaStreamWaitEvent(origin, ev[i], 0));
+  } else {
+    B_CK(cudaEventRecord(ev[n + 1], origin));
+    for (int i = 0; i < n; ++i) {
+      B_CK(cudaStreamWaitEvent(fs[i], ev[n + 1], 0));
+      st = iterate_impl(plans[i], plans[i]->d.iters);
+      if (st != T2SH_OK) {
+        cudaStreamEndCapture(origin, &graph);
+        goto done;
+      }
+      B_CK(cudaEventRecord(ev[i], fs[i]));
+      B_CK(cudaStreamWaitEvent(origin, ev[i], 0));
+    }
   }
   B_CK(cudaStreamEndCapture(origin, &graph));
   B_CK(cudaGraphInstantiate(&exec, graph, 0));
@@ -1051,14 +1173,22 @@ done:
       plans[i]->st = saved[i];
       plans[i]->timing = timing[i];
     }
+  if (origin) cudaStreamSynchronize(origin);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
+  if (bl.dev) cudaFree(bl.dev);
   for (auto& f : fs)
     if (f) cudaStreamDestroy(f);
   if (origin) cudaStreamDestroy(origin);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   return st;
+}
+
+t2sh_status t2sh_batch_schedule(int32_t per_scan_llr) {
+  T2SH_REQ(per_scan_llr == 0 || per_scan_llr == 1, "per_scan_llr must be 0 or 1");
+  g_batch_per_scan_llr = per_scan_llr;
+  return T2SH_OK;
 }
 
 t2sh_status t2sh_objective(t2sh_plan_t p, const void* kspace, int32_t kform, const void* x, double* out) {

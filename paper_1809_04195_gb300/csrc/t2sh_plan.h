@@ -119,6 +119,24 @@ cudaError_t launch_cg_dir(const Geom& g, const float2* r, float2* p, const doubl
 cudaError_t launch_llr(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad,
                        const float2* aty, cudaStream_t st);
 
+// One scan's part of a work-list LLR launch (the FISTA step of several scans in one grid):
+// its geometry, this iteration's arguments and buffers, and its first CTA in the launch.
+struct LlrJob {
+  Geom g;
+  FistaArgs a;
+  float2* x;
+  float2* z;
+  const float2* grad;
+  const float2* aty;
+  int unit0;
+};
+int llr_units(const Geom& g, int b);  // CTAs of one scan's LLR launch
+size_t llr_smem_bytes(const Geom& g, int b);
+// jobs: device array in increasing unit0; units = total CTAs; kc8: some scan has K > 4;
+// smem: the largest llr_smem_bytes of the jobs
+cudaError_t launch_llr_list(const LlrJob* jobs, int njobs, int units, bool kc8, bool eig64, size_t smem,
+                            cudaStream_t st);
+
 // size-specialised passes (k_fft_fast.cu); cudaErrorNotSupported when the shape has none
 cudaError_t launch_row_fast(const Geom& g, RowMode mode, const float2* tw_z, const float2* maps, const float2* x,
                             float2* t, float2* out, cudaStream_t st);

@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "t2sh_solve_batch": [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i32),
                                  ctypes.POINTER(_vp), _vp],
             "t2sh_autotune": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+            "t2sh_batch_schedule": [_i32],
             "t2sh_sync": [_vp],
             "t2sh_configure": [_vp, _i32, _i32],
             "t2sh_wait_selftest": [_vp, _u64],
@@ -248,6 +249,12 @@ def noalloc_wait_selftest(limit_ns: int, stream=None):
     if stream is None:
         stream = torch.cuda.current_stream()
     _check(lib().t2sh_noalloc_wait_selftest(int(limit_ns), ctypes.c_void_p(stream.cuda_stream)))
+
+
+def batch_schedule(per_scan_llr: bool):
+    """solve_batch's LLR schedule: one work-list launch per iteration (False, default) or
+    one launch per plan on its own stream (True)."""
+    _check(lib().t2sh_batch_schedule(1 if per_scan_llr else 0))
 
 
 def solve_batch(plans, kspaces, kforms=None, outs=None, stream=None):

@@ -372,13 +372,36 @@ def test_batch_of_uneven_scans_matches_single_solves(T):
         ks.append(ytil)
         refs.append(O.fista(host(ytil)[S - 1], "proj", maps[S - 1], mask, phi, kw["lam"], kw["block"], kw["iters"],
                             kw["seed"]))
+    for per_scan in (False, True):  # the LLR work list, then one LLR launch per scan
+        T.batch_schedule(per_scan)
+        try:
+            outs = T.solve_batch(plans, ks)
+        finally:
+            T.batch_schedule(False)
+        for o, ref, oref in zip(outs, singles, refs):
+            got = host(o)
+            assert np.array_equal(got, ref)
+            e = nrmse(got[-1], oref)
+            print("batch scan vs oracle NRMSE", e)
+            assert e < SOLVE_TOL
+    for p in plans:
+        p.close()
+
+
+def test_batch_mixing_llr_variants_falls_back_to_per_scan_launches(T):
+    """A batch whose plans take different LLR variants (float64 eigen-step in one of them)
+    runs one LLR launch per scan; results still equal the single solves bitwise."""
+    plans, ks, singles = [], [], []
+    for i, flags in enumerate((0, T.EIG_FP64)):
+        rng, phi, mask, maps = random_problem(230 + i, 2, 64, 48, 3, 12, 4, 1, frac=0.25)
+        ytil = c64(crandn(rng, 2, 3, 4, 64, 48) * 0.05)
+        p = make_plan(T, phi, mask, maps, block=8, lam=0.01, iters=8, seed=11 + i, flags=flags)
+        singles.append(host(p.solve(ytil, T.KSPACE_PROJ)))
+        plans.append(p)
+        ks.append(ytil)
     outs = T.solve_batch(plans, ks)
-    for o, ref, oref in zip(outs, singles, refs):
-        got = host(o)
-        assert np.array_equal(got, ref)
-        e = nrmse(got[-1], oref)
-        print("batch scan vs oracle NRMSE", e)
-        assert e < SOLVE_TOL
+    for o, ref in zip(outs, singles):
+        assert np.array_equal(host(o), ref)
     for p in plans:
         p.close()
 
