@@ -3,8 +3,11 @@
 // list; for each tile one thread issues two 3D tensor-map box copies that complete on
 // mbarriers: the K x ny x 8 block of the intermediate t and the P x ny x 8 block of
 // Psi.  The next tile's t block is requested as soon as the forward stage A has read the
-// current one, the next Psi block right after the Psi step, so both copies overlap the
-// remaining transform work.  Results go straight from registers to global memory.
+// current one.  Once Psi is applied, its block serves as the destination of the inverse
+// stage's transposed lines, so that stage needs no barrier between its reads of the
+// exchange lines and its writes; the next tile's Psi block is requested right after that
+// tile's first wait, which every thread reaches only after reading the scratch.  Five
+// block-wide barriers per tile.  Results go straight from registers to global memory.
 //
 // Transform layout (N = 16 R1): thread (w, j) of basis line k holds column w's
 // x[j + 16 q]; forward [R1, 16] and inverse [16, R1] two-stage transforms as in the
@@ -34,7 +37,13 @@ struct ColTma {
   static constexpr size_t off_ex = ((size_t)N * 8 + 127) / 128 * 128;                       // bytes
   static constexpr size_t off_t = (off_ex + (size_t)4 * W * LS * 8 + 127) / 128 * 128;
   static constexpr size_t off_psi = off_t + (size_t)4 * N * W * 8;
-  static size_t smem(int P) { return off_psi + (size_t)P * N * W * 4 + 64; }
+  // the Psi block also holds the inverse stage's transposed lines once Psi is applied
+  static constexpr size_t ex_bytes = (size_t)4 * W * LS * 8;
+  __host__ __device__ static size_t psi_region(int P) {
+    const size_t pb = ((size_t)P * N * W * 4 + 127) / 128 * 128;
+    return pb > ex_bytes ? pb : (ex_bytes + 127) / 128 * 128;
+  }
+  __host__ __device__ static size_t smem(int P) { return off_psi + psi_region(P) + 64; }
 };
 
 template <int N, int W>
@@ -50,7 +59,7 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
   float2* st = reinterpret_cast<float2*>(smem_raw + CT::off_t);    // [k][y][W] (TMA box)
   float* ps = reinterpret_cast<float*>(smem_raw + CT::off_psi);    // [p][y][W] (TMA box)
   const int nz = g.nz, NN = N * nz, K = g.K, P = g.P;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + (size_t)P * N * W * 4);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + CT::psi_region(P));
   constexpr int JPH = CT::JPH;
   const int w = threadIdx.x & (W - 1), jl = (threadIdx.x >> WL) & (JPH - 1), k = (threadIdx.x >> 4) & 3,
             j = JPH * (threadIdx.x >> 6) + jl;
@@ -73,6 +82,8 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
   }
   unsigned ph_t = 0, ph_p = 0;
   float2* exl = ex + (k * W + w) * LS;
+  float2* oxl = reinterpret_cast<float2*>(ps) + (k * W + w) * LS;  // inverse lines, in the Psi block
+  bool psi_issued = true;  // the first tile's Psi block was requested above
   for (; tile < ntiles; tile += gridDim.x) {
     const int nxt = tile + gridDim.x;
     const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
@@ -81,11 +92,19 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
       if (threadIdx.x == 0) {  // record, then give copies in flight one more bounded wait
         if (g.err) atomicExch(g.err, 1);
         mbar_wait_bounded(&bars[0], ph_t);
-        mbar_wait_bounded(&bars[1], ph_p);
+        if (psi_issued) mbar_wait_bounded(&bars[1], ph_p);
       }
       return;
     }
     ph_t ^= 1;
+    // every thread has left the previous tile's last stage, which read the Psi block as
+    // scratch: this tile's Psi block may land there now
+    if (threadIdx.x == 0 && !psi_issued) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(&bars[1], bytes_p);
+      tma_load_3d(ps, &tm_psi, &bars[1], z0, 0, 0);
+    }
+    psi_issued = true;
     // forward stage A: DFT_R1 of x[j + 16 q]
     if (live) {
       const float2* sp = st + (k * N) * W + w;
@@ -162,36 +181,30 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
           for (int c = 0; c < 4; ++c) ex[(l * W + c0 + c) * LS + pos] = u[l][c];
     }
     __syncthreads();
-    if (threadIdx.x == 0 && nxt < ntiles) {  // the Psi block is consumed: fetch the next one
-      const int zn = (nxt - (nxt / ntz) * ntz) * W;
-      fence_proxy_async_smem();
-      mbar_expect_tx(&bars[1], bytes_p);
-      tma_load_3d(ps, &tm_psi, &bars[1], zn, 0, 0);
-    }
-    // inverse stage A': IDFT_16 of X[j + R1 q], result to [j][r1] (stride 17)
-    float2 b[16];
+    psi_issued = false;  // the Psi block is consumed; the next tile's lands after its first wait
+    // inverse stage A': IDFT_16 of X[j + R1 q], result to [j][r1] (stride 17) in the Psi
+    // block, so no thread's write can overtake another's read of the exchange lines
     if (live && j < R1) {
+      float2 b[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
       dft16<true>(b);
-    }
-    __syncthreads();
-    if (live && j < R1) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) exl[j * SI + q] = b[q];
+      for (int q = 0; q < 16; ++q) oxl[j * SI + q] = b[q];
     }
     __syncthreads();
-    // inverse stage B': twiddle, IDFT_R1 -> y = j + 16 q, straight to global memory
+    // inverse stage B': twiddle, IDFT_R1 -> y = j + 16 q, straight to global memory (the next
+    // tile's first wait, a block-wide barrier, orders these reads before anything overwrites
+    // the exchange lines or the Psi block)
     if (live) {
       float2 a[R1];
 #pragma unroll
-      for (int q = 0; q < R1; ++q) a[q] = twiddle_mul<true>(exl[q * SI + j], tw[q * j]);
+      for (int q = 0; q < R1; ++q) a[q] = twiddle_mul<true>(oxl[q * SI + j], tw[q * j]);
       dft_r<R1, true>(a);
       float2* ob = t + ((long long)sc * K + k) * NN + z0 + w;
 #pragma unroll
       for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
     }
-    __syncthreads();
   }
 }
 
