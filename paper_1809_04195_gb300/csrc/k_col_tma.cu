@@ -208,6 +208,88 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
   }
 }
 
+// A^H y column pass (COL_ADJ_DATA): x[y] = IDFT_y of the projected k-space column scaled by
+// gsign (-1)^(ky + kz) / sqrt(ny nz), from tin to tout.  Same tiles, copies and inverse
+// stages as the normal pass, without the forward transform and Psi: thread (line, j < R1)
+// takes X[j + R1 q] (q < 16) straight from the tile into registers, IDFT_16, transposed
+// lines to the scratch block, then IDFT_R1 to global memory.  Two block-wide barriers per
+// tile; the next tile's copy is requested as soon as the current one has been read.
+template <int N, int W>
+__global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma_adj(Geom g, const __grid_constant__ CUtensorMap tm_in,
+                                                          const float2* __restrict__ tw_g, float2* tout, int ntz,
+                                                          int ntiles) {
+  using CT = ColTma<N, W>;
+  constexpr int R1 = CT::R1, SI = CT::SI, LS = CT::LS;
+  constexpr int WL = W == 8 ? 3 : 2;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* st = reinterpret_cast<float2*>(smem_raw + CT::off_t);                // [k][y][W] (TMA box)
+  float2* ox = reinterpret_cast<float2*>(smem_raw + CT::off_psi);              // [k][w][LS] inverse lines
+  const int nz = g.nz, NN = N * nz, K = g.K;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + CT::off_psi + CT::psi_region(g.P));
+  constexpr int JPH = CT::JPH;
+  const int w = threadIdx.x & (W - 1), jl = (threadIdx.x >> WL) & (JPH - 1), k = (threadIdx.x >> 4) & 3,
+            j = JPH * (threadIdx.x >> 6) + jl;
+  const bool live = k < K;
+  const unsigned bytes_t = (unsigned)(K * N * W * 8);
+  const float scale = g.gsign * g.inv_sqrt_n;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) {
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
+    mbar_expect_tx(&bars[0], bytes_t);
+    tma_load_3d(st, &tm_in, &bars[0], z0, 0, sc * K);
+  }
+  unsigned ph_t = 0;
+  float2* oxl = ox + (k * W + w) * LS;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
+    const bool ok = mbar_wait_bounded(&bars[0], ph_t);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {  // record, then give the copy in flight one more bounded wait
+        if (g.err) atomicExch(g.err, 1);
+        mbar_wait_bounded(&bars[0], ph_t);
+      }
+      return;
+    }
+    ph_t ^= 1;
+    // IDFT_16 over q of the scaled X[j + R1 q], result to [j][r1] (stride 17)
+    if (live && j < R1) {
+      float2 b[16];
+      const float2* sp = st + (k * N + j) * W + w;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = cscale(sp[R1 * q * W], scale * parity_sign(j + R1 * q + z0 + w));
+      dft16<true>(b);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) oxl[j * SI + q] = b[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && nxt < ntiles) {  // the tile is read: fetch the next one
+      const int sn = nxt / ntz, zn = (nxt - sn * ntz) * W;
+      fence_proxy_async_smem();
+      mbar_expect_tx(&bars[0], bytes_t);
+      tma_load_3d(st, &tm_in, &bars[0], zn, 0, sn * K);
+    }
+    // twiddle, IDFT_R1 -> y = j + 16 q (the next tile's first wait orders these reads
+    // before the scratch is written again)
+    if (live) {
+      float2 a[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) a[q] = twiddle_mul<true>(oxl[q * SI + j], tw[q * j]);
+      dft_r<R1, true>(a);
+      float2* ob = tout + ((long long)sc * K + k) * NN + z0 + w;
+#pragma unroll
+      for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
+    }
+  }
+}
+
 // Self-test of the bounded-wait path: one thread waits on an mbarrier that nothing
 // completes, with a limit of limit_ns, and records the timeout in the error flag exactly
 // as the tile kernels do.  Nothing is in flight, so the kernel simply returns.
@@ -292,7 +374,53 @@ cudaError_t col_tma_w(const Geom& g, const float2* tw_y, const float* psi, float
     default: return cudaErrorNotSupported;
   }
 }
+template <int N, int W>
+cudaError_t col_tma_adj_go(const Geom& g, const float2* tw, const float2* tin, float2* tout, cudaStream_t st) {
+  using CT = ColTma<N, W>;
+  TmaEncodeFn enc = tma_encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tm_in;
+  const cuuint64_t dt[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.S * g.C * g.K};
+  const cuuint64_t st_t[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)N * g.nz * 8};
+  const cuuint32_t bt[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)g.K};
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&tm_in, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<float2*>(tin), dt, st_t, bt, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorNotSupported;
+  const size_t sm = CT::smem(g.P);
+  int nsm = 0;
+  {
+    cudaError_t e = smem_optin((const void*)k_col_tma_adj<N, W>, (int)CT::smem(10));
+    if (e == cudaSuccess) e = sm_count(&nsm);
+    if (e != cudaSuccess) return e;
+  }
+  const int ntz = g.nz / W;
+  const long long ntiles = (long long)g.S * g.C * ntz;
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * (8 / W));
+  k_col_tma_adj<N, W><<<grid, 64 * W, sm, st>>>(g, tm_in, tw, tout, ntz, (int)ntiles);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_col_adj_tma(const Geom& g, const float2* tw_y, const float2* tin, float2* tout, cudaStream_t st) {
+  constexpr int W = 8;
+  if (g.K > 4 || g.nz % W != 0) return cudaErrorNotSupported;  // in place is fine: a tile is read whole before it is written
+  switch (g.ny) {
+    case 48: return col_tma_adj_go<48, W>(g, tw_y, tin, tout, st);
+    case 64: return col_tma_adj_go<64, W>(g, tw_y, tin, tout, st);
+    case 96: return col_tma_adj_go<96, W>(g, tw_y, tin, tout, st);
+    case 128: return col_tma_adj_go<128, W>(g, tw_y, tin, tout, st);
+    case 160: return col_tma_adj_go<160, W>(g, tw_y, tin, tout, st);
+    case 192: return col_tma_adj_go<192, W>(g, tw_y, tin, tout, st);
+    case 240: return col_tma_adj_go<240, W>(g, tw_y, tin, tout, st);
+    case 256: return col_tma_adj_go<256, W>(g, tw_y, tin, tout, st);
+    default: return cudaErrorNotSupported;
+  }
+}
 
 cudaError_t launch_col_normal_tma(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st) {
   return g.colvar == 4 ? col_tma_w<4>(g, tw_y, psi, t, st) : col_tma_w<8>(g, tw_y, psi, t, st);

@@ -475,7 +475,10 @@ cudaError_t launch_col(const Geom& g, ColMode mode, const FftPlan& py, const flo
         if (ep != cudaErrorNotSupported) return ep;
       }
       return k4 ? col_normal_go<4>(g, py, tw_y, psi, tout, st) : col_normal_go<8>(g, py, tw_y, psi, tout, st);
-    case COL_ADJ_DATA:
+    case COL_ADJ_DATA: {
+      const cudaError_t et = launch_col_adj_tma(g, tw_y, tin, tout, st);
+      if (et != cudaErrorNotSupported) return et;
+    }
       return k4 ? col_go<COL_ADJ_DATA, 4>(g, py, tw_y, psi, phi, mask, tin, tout, st)
                 : col_go<COL_ADJ_DATA, 8>(g, py, tw_y, psi, phi, mask, tin, tout, st);
     case COL_FWD_PROJ:

@@ -150,6 +150,8 @@ cudaError_t launch_wait_selftest(int* err, unsigned long long limit_ns, cudaStre
 cudaError_t launch_col_normal_pr(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 cudaError_t launch_col_normal_tc(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
 cudaError_t launch_col_normal_tma(const Geom& g, const float2* tw_y, const float* psi, float2* t, cudaStream_t st);
+// A^H y column pass on TMA tiles (K <= 4, nz % 8 == 0, ny = 16 R1 <= 256; tin may equal tout)
+cudaError_t launch_col_adj_tma(const Geom& g, const float2* tw_y, const float2* tin, float2* tout, cudaStream_t st);
 
 // fused row work of one FISTA iteration (k_fused.cu)
 bool band_fused_supported(const Geom& g, int block);
