@@ -62,3 +62,21 @@ def test_algorithmic_bytes_of_the_knee_scan():
     assert ab["row_fwd"] == ab["row_adj"] == pytest.approx(6.71e9, rel=2e-3)
     assert ab["col"] == pytest.approx(10.07e9, rel=2e-3)
     assert ab["llr"] == pytest.approx(2.52e9, rel=2e-3)
+
+
+def test_cpu_sample_is_seeded_distinct_and_stable():
+    """The oracle's timing sample: 8 distinct slices of the scan, the same every run."""
+    import t2sh_synth as synth
+    a = bench.sample_slices(synth.KNEE_320x256x160)
+    b = bench.sample_slices(synth.KNEE_320x256x160)
+    assert a == b and len(a) == bench.CPU_SAMPLE_SLICES == len(set(a))
+    assert a == sorted(a) and 0 <= a[0] and a[-1] < 320
+    assert bench.sample_slices(synth.PAPER_288x260x240) != a
+    assert bench.shape_by_name(bench.shape_name(synth.PAPER_288x260x240)) is synth.PAPER_288x260x240
+
+
+def test_batch3_config_names_the_three_scans():
+    import t2sh_synth as synth
+    c = bench.batch3_config(1)
+    assert c["slices"] == sum(sh.nslices for sh in synth.BATCH_SCANS) == 864
+    assert len(c["scans"]) == 3 and "256x160 C=12" in c["workload"] and "192x192 C=16" in c["workload"]

@@ -118,3 +118,12 @@ def test_wavelet_denoise_rejects_bad_arguments(T):
         assert ei.value.status == T.EINVAL
         p.wavelet_denoise(x, 0.1, 1)  # 6, 16, 24 are even: one level works
         p.sync()
+        lib = T.lib()
+        import ctypes
+        st = lib.t2sh_wavelet_denoise(p._h, ctypes.c_void_p(x.data_ptr() + 8), ctypes.c_float(0.1), 1)
+        assert st == T.EINVAL and "aligned" in T.last_error()  # 8 bytes off a 16-byte boundary
+    d = T.make_dims(16, 24, 2, 8, 2, nslices=6, flags=T.HOST_IO)
+    with T.Plan(d, phi.astype(np.float32), mask, maps.astype(np.complex64)) as p:
+        with pytest.raises(T.T2shError) as ei:
+            p.wavelet_denoise(torch.zeros((6, 1, 2, 16, 24), dtype=torch.complex64, device="cuda"), 0.1, 1)
+        assert ei.value.status == T.EUNSUPPORTED
