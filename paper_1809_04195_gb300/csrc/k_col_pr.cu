@@ -7,8 +7,9 @@
 //   inverse:  thread k1 < R1: IDFT_P over k2 of X[k1 + R1 k2] -> Z[k1][j] (stride P + 1);
 //             thread j: twiddle w_N^(-k1 j), IDFT_R1 over k1 -> x[j + P q], straight to memory.
 // Persistent CTAs of W x 4 x P threads over (slice, coil, W-column tile) tiles; the tile and
-// its Psi block are staged by cp.async (a 260-row column exceeds the 256-element box of a
-// tensor-map copy), the next tile's copies issued as soon as the staging area is free.
+// its Psi block are staged by cp.async, the next tile's copies issued as soon as the staging
+// area is free.  (The TMA column kernels copy a 260-row column as two tensor-map boxes;
+// this kernel serves the cp.async column variants at this length.)
 // R1 odd (the stage-A exchange stride), K <= 4, nz % W == 0.
 #include <algorithm>
 

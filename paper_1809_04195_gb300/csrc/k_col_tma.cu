@@ -9,12 +9,15 @@
 // tile's first wait, which every thread reaches only after reading the scratch.  Five
 // block-wide barriers per tile.  Results go straight from registers to global memory.
 //
-// Transform layout (N = 16 R1): thread (w, j) of basis line k holds column w's
-// x[j + 16 q]; forward [R1, 16] and inverse [16, R1] two-stage transforms as in the
-// size-specialised kernels.  A half-warp spans the 8 columns x 2 consecutive j of one
-// basis line, the exchange lines are padded to a stride = 2 (mod 16) float2 and the
-// in-line layouts use odd strides, so every shared-memory access of the kernel is free
-// of bank conflicts.  Requires nz % 8 == 0, K <= 4, ny = N <= 256.
+// Transform layout (N = P R1 with P = 16, or P = 20 for the 260-point lines of Table I):
+// thread (w, j < P) of basis line k holds column w's x[j + P q]; forward [R1, P] and
+// inverse [P, R1] two-stage transforms as in the size-specialised kernels.  A half-warp
+// spans the W columns x 16 / W consecutive j of one basis line, the exchange lines are
+// padded to a stride = 16 / W (mod 16) float2 and the in-line layouts use odd strides, so
+// every shared-memory access of the kernel is free of bank conflicts.  A column longer
+// than a tensor-map box (256 rows) is copied as two halves by a 4D map whose two middle
+// dimensions split y, landing in the same [k][y][w] layout.  Requires nz % W == 0, K <= 4,
+// ny = N <= 256 or N = 260.
 #include <cuda.h>
 
 #include <algorithm>
@@ -26,10 +29,15 @@ namespace t2sh {
 
 template <int N, int W>
 struct ColTma {
-  static constexpr int R1 = N / 16;
-  static constexpr int SF = ExLayout<R1>::SF;  // forward in-line stride (odd)
-  static constexpr int SI = 17;                // inverse in-line stride (odd)
-  static constexpr int LINE = ExLayout<R1>::LINE;
+  static constexpr int P = N % 16 == 0 ? 16 : 20;  // stage-A threads per line = stage-B radix
+  static constexpr int R1 = N / P;
+  static_assert(P * R1 == N, "N = 16 R1 or 20 R1");
+  static constexpr int SF = (R1 % 2) ? R1 : R1 + 1;  // forward in-line stride (odd)
+  static constexpr int SI = P + 1;                   // inverse in-line stride (odd)
+  static constexpr int LINE = (P * SF > R1 * SI) ? P * SF : R1 * SI;
+  static constexpr int THREADS = 4 * W * P;
+  static constexpr int MINB = 8 / W;                             // CTAs per SM the shared memory allows
+  static constexpr bool Y4D = N > 256;                          // y split over two box dimensions
   // a half-warp holds W columns x JPH = 16 / W consecutive j; the exchange line stride
   // LS = JPH (mod 16) with SF = 1 (mod 16) spreads its accesses over all banks
   static constexpr int JPH = 16 / W;
@@ -46,12 +54,22 @@ struct ColTma {
   __host__ __device__ static size_t smem(int P) { return off_psi + psi_region(P) + 64; }
 };
 
+// the tile's rows row0 .. row0 + box - 1 of columns z0 .. z0 + W - 1 (3D map, or 4D with y
+// split in halves)
+template <bool Y4D>
+__device__ __forceinline__ void tma_tile(void* dst, const CUtensorMap* m, unsigned long long* bar, int z0, int row0) {
+  if constexpr (Y4D)
+    tma_load_4d(dst, m, bar, z0, 0, 0, row0);
+  else
+    tma_load_3d(dst, m, bar, z0, 0, row0);
+}
+
 template <int N, int W>
-__global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_constant__ CUtensorMap tm_t,
+__global__ void __launch_bounds__(ColTma<N, W>::THREADS, ColTma<N, W>::MINB) k_col_tma(Geom g, const __grid_constant__ CUtensorMap tm_t,
                                                    const __grid_constant__ CUtensorMap tm_psi,
                                                    const float2* __restrict__ tw_g, float2* t, int ntz, int ntiles) {
   using CT = ColTma<N, W>;
-  constexpr int R1 = CT::R1, SF = CT::SF, SI = CT::SI, LS = CT::LS;
+  constexpr int P1 = CT::P, R1 = CT::R1, SF = CT::SF, SI = CT::SI, LS = CT::LS;
   constexpr int WL = W == 8 ? 3 : 2;  // log2 W
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
@@ -76,9 +94,9 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
   if (threadIdx.x == 0 && tile < ntiles) {
     const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
     mbar_expect_tx(&bars[0], bytes_t);
-    tma_load_3d(st, &tm_t, &bars[0], z0, 0, sc * K);
+    tma_tile<CT::Y4D>(st, &tm_t, &bars[0], z0, sc * K);
     mbar_expect_tx(&bars[1], bytes_p);
-    tma_load_3d(ps, &tm_psi, &bars[1], z0, 0, 0);
+    tma_tile<CT::Y4D>(ps, &tm_psi, &bars[1], z0, 0);
   }
   unsigned ph_t = 0, ph_p = 0;
   float2* exl = ex + (k * W + w) * LS;
@@ -102,15 +120,15 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
     if (threadIdx.x == 0 && !psi_issued) {
       fence_proxy_async_smem();
       mbar_expect_tx(&bars[1], bytes_p);
-      tma_load_3d(ps, &tm_psi, &bars[1], z0, 0, 0);
+      tma_tile<CT::Y4D>(ps, &tm_psi, &bars[1], z0, 0);
     }
     psi_issued = true;
-    // forward stage A: DFT_R1 of x[j + 16 q]
+    // forward stage A: DFT_R1 of x[j + P q]
     if (live) {
       const float2* sp = st + (k * N) * W + w;
       float2 a[R1];
 #pragma unroll
-      for (int q = 0; q < R1; ++q) a[q] = sp[(j + 16 * q) * W];
+      for (int q = 0; q < R1; ++q) a[q] = sp[(j + P1 * q) * W];
       dft_r<R1, false>(a);
 #pragma unroll
       for (int q = 0; q < R1; ++q) exl[j * SF + q] = a[q];
@@ -120,18 +138,18 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
       const int sn = nxt / ntz, zn = (nxt - sn * ntz) * W;
       fence_proxy_async_smem();
       mbar_expect_tx(&bars[0], bytes_t);
-      tma_load_3d(st, &tm_t, &bars[0], zn, 0, sn * K);
+      tma_tile<CT::Y4D>(st, &tm_t, &bars[0], zn, sn * K);
     }
-    // forward stage B: twiddle, DFT_16 -> X[j + R1 q] at [q][j]
+    // forward stage B: twiddle, DFT_P -> X[j + R1 q] at [q][j]
     if (live && j < R1) {
-      float2 b[16];
+      float2 b[P1];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
+      for (int q = 0; q < P1; ++q) b[q] = exl[q * SF + j];
 #pragma unroll
-      for (int q = 1; q < 16; ++q) b[q] = twiddle_mul<false>(b[q], tw[q * j]);
-      dft16<false>(b);
+      for (int q = 1; q < P1; ++q) b[q] = twiddle_mul<false>(b[q], tw[q * j]);
+      dft_r<P1, false>(b);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) exl[q * SF + j] = b[q];
+      for (int q = 0; q < P1; ++q) exl[q * SF + j] = b[q];
     }
     ok = mbar_wait_bounded(&bars[1], ph_p);
     if (__syncthreads_or(!ok)) {
@@ -182,18 +200,18 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
     }
     __syncthreads();
     psi_issued = false;  // the Psi block is consumed; the next tile's lands after its first wait
-    // inverse stage A': IDFT_16 of X[j + R1 q], result to [j][r1] (stride 17) in the Psi
+    // inverse stage A': IDFT_P of X[j + R1 q], result to [j][r1] (stride P + 1) in the Psi
     // block, so no thread's write can overtake another's read of the exchange lines
     if (live && j < R1) {
-      float2 b[16];
+      float2 b[P1];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) b[q] = exl[q * SF + j];
-      dft16<true>(b);
+      for (int q = 0; q < P1; ++q) b[q] = exl[q * SF + j];
+      dft_r<P1, true>(b);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) oxl[j * SI + q] = b[q];
+      for (int q = 0; q < P1; ++q) oxl[j * SI + q] = b[q];
     }
     __syncthreads();
-    // inverse stage B': twiddle, IDFT_R1 -> y = j + 16 q, straight to global memory (the next
+    // inverse stage B': twiddle, IDFT_R1 -> y = j + P q, straight to global memory (the next
     // tile's first wait, a block-wide barrier, orders these reads before anything overwrites
     // the exchange lines or the Psi block)
     if (live) {
@@ -203,7 +221,7 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
       dft_r<R1, true>(a);
       float2* ob = t + ((long long)sc * K + k) * NN + z0 + w;
 #pragma unroll
-      for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
+      for (int q = 0; q < R1; ++q) ob[(long long)(j + P1 * q) * nz] = a[q];
     }
   }
 }
@@ -211,15 +229,15 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma(Geom g, const __grid_
 // A^H y column pass (COL_ADJ_DATA): x[y] = IDFT_y of the projected k-space column scaled by
 // gsign (-1)^(ky + kz) / sqrt(ny nz), from tin to tout.  Same tiles, copies and inverse
 // stages as the normal pass, without the forward transform and Psi: thread (line, j < R1)
-// takes X[j + R1 q] (q < 16) straight from the tile into registers, IDFT_16, transposed
+// takes X[j + R1 q] (q < P) straight from the tile into registers, IDFT_P, transposed
 // lines to the scratch block, then IDFT_R1 to global memory.  Two block-wide barriers per
 // tile; the next tile's copy is requested as soon as the current one has been read.
 template <int N, int W>
-__global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma_adj(Geom g, const __grid_constant__ CUtensorMap tm_in,
+__global__ void __launch_bounds__(ColTma<N, W>::THREADS, ColTma<N, W>::MINB) k_col_tma_adj(Geom g, const __grid_constant__ CUtensorMap tm_in,
                                                           const float2* __restrict__ tw_g, float2* tout, int ntz,
                                                           int ntiles) {
   using CT = ColTma<N, W>;
-  constexpr int R1 = CT::R1, SI = CT::SI, LS = CT::LS;
+  constexpr int P1 = CT::P, R1 = CT::R1, SI = CT::SI, LS = CT::LS;
   constexpr int WL = W == 8 ? 3 : 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma_adj(Geom g, const __g
   if (threadIdx.x == 0 && tile < ntiles) {
     const int sc = tile / ntz, z0 = (tile - sc * ntz) * W;
     mbar_expect_tx(&bars[0], bytes_t);
-    tma_load_3d(st, &tm_in, &bars[0], z0, 0, sc * K);
+    tma_tile<CT::Y4D>(st, &tm_in, &bars[0], z0, sc * K);
   }
   unsigned ph_t = 0;
   float2* oxl = ox + (k * W + w) * LS;
@@ -259,24 +277,24 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma_adj(Geom g, const __g
       return;
     }
     ph_t ^= 1;
-    // IDFT_16 over q of the scaled X[j + R1 q], result to [j][r1] (stride 17)
+    // IDFT_P over q of the scaled X[j + R1 q], result to [j][r1] (stride P + 1)
     if (live && j < R1) {
-      float2 b[16];
+      float2 b[P1];
       const float2* sp = st + (k * N + j) * W + w;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) b[q] = cscale(sp[R1 * q * W], scale * parity_sign(j + R1 * q + z0 + w));
-      dft16<true>(b);
+      for (int q = 0; q < P1; ++q) b[q] = cscale(sp[R1 * q * W], scale * parity_sign(j + R1 * q + z0 + w));
+      dft_r<P1, true>(b);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) oxl[j * SI + q] = b[q];
+      for (int q = 0; q < P1; ++q) oxl[j * SI + q] = b[q];
     }
     __syncthreads();
     if (threadIdx.x == 0 && nxt < ntiles) {  // the tile is read: fetch the next one
       const int sn = nxt / ntz, zn = (nxt - sn * ntz) * W;
       fence_proxy_async_smem();
       mbar_expect_tx(&bars[0], bytes_t);
-      tma_load_3d(st, &tm_in, &bars[0], zn, 0, sn * K);
+      tma_tile<CT::Y4D>(st, &tm_in, &bars[0], zn, sn * K);
     }
-    // twiddle, IDFT_R1 -> y = j + 16 q (the next tile's first wait orders these reads
+    // twiddle, IDFT_R1 -> y = j + P q (the next tile's first wait orders these reads
     // before the scratch is written again)
     if (live) {
       float2 a[R1];
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(64 * W, 8 / W) k_col_tma_adj(Geom g, const __g
       dft_r<R1, true>(a);
       float2* ob = tout + ((long long)sc * K + k) * NN + z0 + w;
 #pragma unroll
-      for (int q = 0; q < R1; ++q) ob[(long long)(j + 16 * q) * nz] = a[q];
+      for (int q = 0; q < R1; ++q) ob[(long long)(j + P1 * q) * nz] = a[q];
     }
   }
 }
@@ -324,25 +342,38 @@ TmaEncodeFn tma_encode_fn() {
 }
 
 namespace {
+// Tensor map of a [rows][N][nz] array of esize-byte elements with W x N x box_rows boxes;
+// for N > 256 the y dimension is split into two halves of N / 2 (4D map, same box layout)
+template <int N, int W>
+bool encode_columns(TmaEncodeFn enc, CUtensorMap* m, CUtensorMapDataType type, const void* base, int nz,
+                    long long rows, int esize, int box_rows) {
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if constexpr (N > 256) {
+    static_assert(N % 2 == 0 && N / 2 <= 256, "two boxes per column");
+    const cuuint64_t d[4] = {(cuuint64_t)nz, (cuuint64_t)(N / 2), 2, (cuuint64_t)rows};
+    const cuuint64_t s[3] = {(cuuint64_t)nz * esize, (cuuint64_t)(N / 2) * nz * esize, (cuuint64_t)N * nz * esize};
+    const cuuint32_t b[4] = {(cuuint32_t)W, (cuuint32_t)(N / 2), 2, (cuuint32_t)box_rows};
+    return enc(m, type, 4, const_cast<void*>(base), d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  } else {
+    const cuuint64_t d[3] = {(cuuint64_t)nz, (cuuint64_t)N, (cuuint64_t)rows};
+    const cuuint64_t s[2] = {(cuuint64_t)nz * esize, (cuuint64_t)N * nz * esize};
+    const cuuint32_t b[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)box_rows};
+    return enc(m, type, 3, const_cast<void*>(base), d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+}
+
 template <int N, int W>
 cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2* t, cudaStream_t st) {
   using CT = ColTma<N, W>;
   TmaEncodeFn enc = tma_encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tm_t, tm_psi;
-  const cuuint64_t dt[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.S * g.C * g.K};
-  const cuuint64_t st_t[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)N * g.nz * 8};
-  const cuuint32_t bt[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)g.K};
-  const cuuint32_t es[3] = {1, 1, 1};
-  if (enc(&tm_t, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, t, dt, st_t, bt, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaErrorNotSupported;
-  const cuuint64_t dp[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.P};
-  const cuuint64_t sp[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)N * g.nz * 4};
-  const cuuint32_t bp[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)g.P};
-  if (enc(&tm_psi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(psi), dp, sp, bp, es,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  if (!encode_columns<N, W>(enc, &tm_t, CU_TENSOR_MAP_DATA_TYPE_INT64, t, g.nz, (long long)g.S * g.C * g.K, 8, g.K) ||
+      !encode_columns<N, W>(enc, &tm_psi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, psi, g.nz, g.P, 4, g.P))
     return cudaErrorNotSupported;
   const size_t sm = CT::smem(g.P);
   int nsm = 0;
@@ -354,8 +385,8 @@ cudaError_t col_tma_go(const Geom& g, const float2* tw, const float* psi, float2
   const int ntz = g.nz / W;
   const long long ntiles = (long long)g.S * g.C * ntz;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * (8 / W));
-  k_col_tma<N, W><<<grid, 64 * W, sm, st>>>(g, tm_t, tm_psi, tw, t, ntz, (int)ntiles);
+  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * CT::MINB);
+  k_col_tma<N, W><<<grid, CT::THREADS, sm, st>>>(g, tm_t, tm_psi, tw, t, ntz, (int)ntiles);
   return cudaGetLastError();
 }
 
@@ -371,6 +402,7 @@ cudaError_t col_tma_w(const Geom& g, const float2* tw_y, const float* psi, float
     case 192: return col_tma_go<192, W>(g, tw_y, psi, t, st);
     case 240: return col_tma_go<240, W>(g, tw_y, psi, t, st);
     case 256: return col_tma_go<256, W>(g, tw_y, psi, t, st);
+    case 260: return col_tma_go<260, W>(g, tw_y, psi, t, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -380,13 +412,7 @@ cudaError_t col_tma_adj_go(const Geom& g, const float2* tw, const float2* tin, f
   TmaEncodeFn enc = tma_encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tm_in;
-  const cuuint64_t dt[3] = {(cuuint64_t)g.nz, (cuuint64_t)N, (cuuint64_t)g.S * g.C * g.K};
-  const cuuint64_t st_t[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)N * g.nz * 8};
-  const cuuint32_t bt[3] = {(cuuint32_t)W, (cuuint32_t)N, (cuuint32_t)g.K};
-  const cuuint32_t es[3] = {1, 1, 1};
-  if (enc(&tm_in, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<float2*>(tin), dt, st_t, bt, es,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  if (!encode_columns<N, W>(enc, &tm_in, CU_TENSOR_MAP_DATA_TYPE_INT64, tin, g.nz, (long long)g.S * g.C * g.K, 8, g.K))
     return cudaErrorNotSupported;
   const size_t sm = CT::smem(g.P);
   int nsm = 0;
@@ -399,8 +425,8 @@ cudaError_t col_tma_adj_go(const Geom& g, const float2* tw, const float2* tin, f
   const long long ntiles = (long long)g.S * g.C * ntz;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (ntiles == 0) return cudaSuccess;
-  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * (8 / W));
-  k_col_tma_adj<N, W><<<grid, 64 * W, sm, st>>>(g, tm_in, tw, tout, ntz, (int)ntiles);
+  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * CT::MINB);
+  k_col_tma_adj<N, W><<<grid, CT::THREADS, sm, st>>>(g, tm_in, tw, tout, ntz, (int)ntiles);
   return cudaGetLastError();
 }
 
@@ -418,6 +444,7 @@ cudaError_t launch_col_adj_tma(const Geom& g, const float2* tw_y, const float2* 
     case 192: return col_tma_adj_go<192, W>(g, tw_y, tin, tout, st);
     case 240: return col_tma_adj_go<240, W>(g, tw_y, tin, tout, st);
     case 256: return col_tma_adj_go<256, W>(g, tw_y, tin, tout, st);
+    case 260: return col_tma_adj_go<260, W>(g, tw_y, tin, tout, st);
     default: return cudaErrorNotSupported;
   }
 }

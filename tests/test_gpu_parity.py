@@ -87,6 +87,7 @@ SHAPES = [
     (1, 192, 192, 2, 12, 4, 2),  # two map sets on the specialised passes
     (2, 96, 64, 2, 8, 2, 1),     # K = 2 on the specialised passes
     (1, 260, 240, 7, 16, 4, 2),  # Table I slice matrix: radix-13 passes, C = 7, M = 2
+    (1, 260, 48, 2, 8, 2, 1),    # 260-point columns (two tensor-map boxes) with K = 2
     (1, 512, 512, 2, 8, 4, 1),   # the largest slice matrix (generic passes)
     (1, 32, 24, 2, 16, 8, 1),    # K = 8, the largest basis
     (2, 8, 8, 1, 4, 2, 1),       # the smallest matrix, one coil
@@ -451,12 +452,14 @@ def test_autotuned_plan_still_matches_oracle(T):
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 4])
-@pytest.mark.parametrize("ny,nz,K", [(256, 160, 4), (256, 160, 2), (240, 128, 3), (64, 48, 4), (96, 36, 2), (192, 64, 4),
-                                     (240, 96, 4), (48, 40, 4), (128, 24, 4), (96, 16, 4), (160, 8, 4)])
+@pytest.mark.parametrize("ny,nz,K", [(256, 160, 4), (256, 160, 2), (260, 240, 4), (260, 40, 3), (240, 128, 3),
+                                     (64, 48, 4), (96, 36, 2), (192, 64, 4), (240, 96, 4), (48, 40, 4), (128, 24, 4),
+                                     (96, 16, 4), (160, 8, 4)])
 def test_column_variants_match_oracle(T, variant, ny, nz, K):
     """Every normal-operator column-pass variant (TMA x8, cp.async x8, cp.async x4, TMA x4)
     on every size-specialised column length; nz = 36 is not a multiple of 8, so the
-    8-column variants fall back there."""
+    8-column variants fall back there.  At 260 rows the TMA variants copy each column as two
+    boxes and the cp.async variants run the 20 x 13 kernel."""
     rng, phi, mask, maps = random_problem(300 + ny + variant, 2, ny, nz, 3, 12, K, 1)
     x = crandn(rng, 2, 1, K, ny, nz)
     with make_plan(T, phi, mask, maps) as p:
