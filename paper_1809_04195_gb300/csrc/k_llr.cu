@@ -263,12 +263,14 @@ __host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
 // The K <= 4 float32 variant is held to 80 registers (three CTAs per SM) or, where four
 // CTAs' shared memory fits on an SM, to 64 registers (four per SM; a few values spill to
 // L1), so that the single-thread eigen-steps of one band overlap the memory phases of the
-// others: 0.735 -> 0.649 ms on the knee scan with four.
+// others: 0.735 -> 0.649 ms on the knee scan with four.  Where a band is so large that only
+// two CTAs fit (the 12-row bands of Table I's 260 x 240 slices), the CTAs have 512 threads
+// at 64 registers, so the memory phases keep as many loads in flight.
 // MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
 // z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
 // u <- w - v.
 // One CTA's work: unit = (slice s, map set m0, band) decoded by llr_unit.
-template <int KC, int MODE, typename ET>
+template <int KC, int MODE, typename ET, int NT>
 __device__ __forceinline__ void llr_band(const Geom& g, const FistaArgs& a, int unit, float2* x, float2* z,
                                          const float2* __restrict__ grad, const float2* __restrict__ aty, float2* u) {
   extern __shared__ float2 smem[];
@@ -277,11 +279,11 @@ __device__ __forceinline__ void llr_band(const Geom& g, const FistaArgs& a, int 
   float2* gs = smem;                                         // [K][rb][llr_ld(nz)]
   float2* wm = gs + (size_t)g.K * un.rb * llr_ld(g.nz);      // [nbz][kWStride]: KC x KC weights
   float* gram = reinterpret_cast<float*>(wm + (size_t)nbz * kWStride<KC>);  // [nbz][kGramStride]
-  llr_gather<MODE>(g, a, un, gs, x, z, grad, aty, u, 0, kThreads);
+  llr_gather<MODE>(g, a, un, gs, x, z, grad, aty, u, 0, NT);
   __syncthreads();
-  llr_gram<KC>(g, a, un, gs, gram, 0, kThreads / 32);
+  llr_gram<KC>(g, a, un, gs, gram, 0, NT / 32);
   __syncthreads();
-  llr_eigen<KC, ET>(gram, a.tau, wm, nbz, 0, kThreads);
+  llr_eigen<KC, ET>(gram, a.tau, wm, nbz, 0, NT);
   __syncthreads();
   const bool want_res = (MODE == LLR_FISTA || MODE == LLR_ADMM) && a.res != nullptr;
   float d2 = 0.f, x2 = 0.f;
@@ -289,46 +291,49 @@ __device__ __forceinline__ void llr_band(const Geom& g, const FistaArgs& a, int 
   if (want_res) llr_res_flush(a.res, d2, x2);
 }
 
-template <int KC, int MODE, typename ET, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
+template <int KC, int MODE, typename ET, int MINB, int NT = kThreads>
+__global__ void __launch_bounds__(NT, MINB)
     k_llr(Geom g, FistaArgs a, float2* x, float2* z, const float2* __restrict__ grad,
           const float2* __restrict__ aty, float2* u) {
   const int nbands = (g.ny + a.b - 1) / a.b;
-  llr_band<KC, MODE, ET>(g, a, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x, x, z, grad, aty, u);
+  llr_band<KC, MODE, ET, NT>(g, a, (blockIdx.y * g.M + blockIdx.z) * nbands + blockIdx.x, x, z, grad, aty, u);
 }
 
 // Work-list form for batched solves: one launch runs the FISTA LLR step of several scans;
 // CTA i belongs to the last job whose first unit is <= i (jobs in increasing unit0).
-template <int KC, typename ET, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_llr_list(const LlrJob* __restrict__ jobs, int njobs) {
+template <int KC, typename ET, int MINB, int NT = kThreads>
+__global__ void __launch_bounds__(NT, MINB) k_llr_list(const LlrJob* __restrict__ jobs, int njobs) {
   int j = 0;
   while (j + 1 < njobs && jobs[j + 1].unit0 <= (int)blockIdx.x) ++j;
   const Geom g = jobs[j].g;
   const FistaArgs a = jobs[j].a;
-  llr_band<KC, LLR_FISTA, ET>(g, a, (int)blockIdx.x - jobs[j].unit0, jobs[j].x, jobs[j].z, jobs[j].grad,
-                              jobs[j].aty, nullptr);
+  llr_band<KC, LLR_FISTA, ET, NT>(g, a, (int)blockIdx.x - jobs[j].unit0, jobs[j].x, jobs[j].z, jobs[j].grad,
+                                  jobs[j].aty, nullptr);
 }
 
-template <int KC, int MODE, typename ET, int MINB>
+template <int KC, int MODE, typename ET, int MINB, int NT = kThreads>
 cudaError_t llr_launch(const Geom& g, const FistaArgs& a, size_t sm, float2* x, float2* z, const float2* grad,
                        const float2* aty, float2* u, cudaStream_t st) {
   {
-    const cudaError_t e = smem_optin((const void*)k_llr<KC, MODE, ET, MINB>, 200 * 1024);
+    const cudaError_t e = smem_optin((const void*)k_llr<KC, MODE, ET, MINB, NT>, 200 * 1024);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((g.ny + a.b - 1) / a.b, g.S, g.M);
-  k_llr<KC, MODE, ET, MINB><<<grid, kThreads, sm, st>>>(g, a, x, z, grad, aty, u);
+  k_llr<KC, MODE, ET, MINB, NT><<<grid, NT, sm, st>>>(g, a, x, z, grad, aty, u);
   return cudaGetLastError();
 }
+
+// CTAs per SM whose shared memory (plus the 1 KB each reserves) fits in 228 KB
+constexpr bool llr_fits(size_t sm, int n) { return (size_t)n * (sm + 1024) <= (size_t)228 * 1024; }
 
 template <int KC, int MODE, typename ET>
 cudaError_t llr_go(const Geom& g, const FistaArgs& a, float2* x, float2* z, const float2* grad, const float2* aty,
                    float2* u, cudaStream_t st) {
   const size_t sm = llr_unit_bytes<KC>(g.K, a.b, g.nz);
   if constexpr (KC == 4 && sizeof(ET) == 4) {
-    // four CTAs per SM where their shared memory (plus the 1 KB each reserves) fits in 228 KB
-    if (4 * (sm + 1024) <= 228 * 1024) return llr_launch<KC, MODE, ET, 4>(g, a, sm, x, z, grad, aty, u, st);
-    return llr_launch<KC, MODE, ET, 3>(g, a, sm, x, z, grad, aty, u, st);
+    if (llr_fits(sm, 4)) return llr_launch<KC, MODE, ET, 4>(g, a, sm, x, z, grad, aty, u, st);
+    if (llr_fits(sm, 3)) return llr_launch<KC, MODE, ET, 3>(g, a, sm, x, z, grad, aty, u, st);
+    return llr_launch<KC, MODE, ET, 2, 2 * kThreads>(g, a, sm, x, z, grad, aty, u, st);
   } else {
     return llr_launch<KC, MODE, ET, 1>(g, a, sm, x, z, grad, aty, u, st);
   }
@@ -362,18 +367,18 @@ int llr_units(const Geom& g, int b) { return ((g.ny + b - 1) / b) * g.S * g.M; }
 cudaError_t launch_llr_list(const LlrJob* jobs, int njobs, int units, bool kc8, bool eig64, size_t smem,
                             cudaStream_t st) {
   if (njobs <= 0 || units <= 0) return cudaSuccess;
-  auto go = [&](auto kern, int minb_unused) -> cudaError_t {
-    (void)minb_unused;
+  auto go = [&](auto kern, int nt) -> cudaError_t {
     const cudaError_t e = smem_optin((const void*)kern, 200 * 1024);
     if (e != cudaSuccess) return e;
-    kern<<<units, kThreads, smem, st>>>(jobs, njobs);
+    kern<<<units, nt, smem, st>>>(jobs, njobs);
     return cudaGetLastError();
   };
-  // the same register bounds as the per-scan launches (llr_go)
-  if (eig64) return kc8 ? go(k_llr_list<8, double, 1>, 1) : go(k_llr_list<4, double, 1>, 1);
-  if (kc8) return go(k_llr_list<8, float, 1>, 1);
-  if (4 * (smem + 1024) <= 228 * 1024) return go(k_llr_list<4, float, 4>, 4);
-  return go(k_llr_list<4, float, 3>, 3);
+  // the same register bounds and CTA sizes as the per-scan launches (llr_go)
+  if (eig64) return kc8 ? go(k_llr_list<8, double, 1>, kThreads) : go(k_llr_list<4, double, 1>, kThreads);
+  if (kc8) return go(k_llr_list<8, float, 1>, kThreads);
+  if (llr_fits(smem, 4)) return go(k_llr_list<4, float, 4>, kThreads);
+  if (llr_fits(smem, 3)) return go(k_llr_list<4, float, 3>, kThreads);
+  return go(k_llr_list<4, float, 2, 2 * kThreads>, 2 * kThreads);
 }
 
 size_t llr_smem_bytes(const Geom& g, int b) {

@@ -389,6 +389,34 @@ def test_batch_of_uneven_scans_matches_single_solves(T):
         p.close()
 
 
+def test_batch_with_table1_bands_matches_single_solves(T):
+    """A scan with Table I's LLR bands (260 x 240, 12-row bands, two map sets: only two band
+    CTAs fit an SM, so the LLR runs 512-thread CTAs) batched with a small scan: the work-list
+    launch takes the large band's CTA shape for both; results equal the single solves (each
+    with its own CTA shape) bitwise, and the large scan's last slice matches the oracle."""
+    shapes = [(2, 260, 240, 2, 12, 4, 2, 12), (2, 64, 48, 3, 12, 4, 1, 8)]
+    plans, ks, singles = [], [], []
+    ref = None
+    for i, (S, ny, nz, C, Tn, K, M, b) in enumerate(shapes):
+        rng, phi, mask, maps = random_problem(260 + i, S, ny, nz, C, Tn, K, M, frac=0.25)
+        ytil = c64(crandn(rng, S, C, K, ny, nz) * 0.05)
+        kw = dict(block=b, lam=0.01, iters=6, seed=7 + i)
+        p = make_plan(T, phi, mask, maps, **kw)
+        singles.append(host(p.solve(ytil, T.KSPACE_PROJ)))
+        plans.append(p)
+        ks.append(ytil)
+        if i == 0:
+            ref = O.fista(host(ytil)[S - 1], "proj", maps[S - 1], mask, phi, kw["lam"], b, kw["iters"], kw["seed"])
+    outs = T.solve_batch(plans, ks)
+    for o, single in zip(outs, singles):
+        assert np.array_equal(host(o), single)
+    e = nrmse(host(outs[0])[-1], ref)
+    print("Table I bands in a batch vs oracle NRMSE", e)
+    assert e < SOLVE_TOL
+    for p in plans:
+        p.close()
+
+
 def test_batch_mixing_llr_variants_falls_back_to_per_scan_launches(T):
     """A batch whose plans take different LLR variants (float64 eigen-step in one of them)
     runs one LLR launch per scan; results still equal the single solves bitwise."""
