@@ -200,6 +200,12 @@ __device__ __forceinline__ void llr_apply(const Geom& g, const FistaArgs& a, con
       xv[k] = (k < K) ? *reinterpret_cast<const float4*>(gs + (k * rb + r) * llr_ld(nz) + zz)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
     const long long gb = gb0 + (long long)y * nz;
+    float4 xp[KC];  // x_k of the pair in every basis image, requested before any store of the row
+    if (MODE == LLR_FISTA) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        xp[k] = (k < K) ? *reinterpret_cast<const float4*>(x + gb + (long long)k * N) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       if (k < K) {
@@ -224,7 +230,7 @@ __device__ __forceinline__ void llr_apply(const Geom& g, const FistaArgs& a, con
           continue;
         }
         if (MODE == LLR_FISTA) {
-          const float4 xo = *reinterpret_cast<const float4*>(x + gi);
+          const float4 xo = xp[k];
           const float4 dx = make_float4(o.x - xo.x, o.y - xo.y, o.z - xo.z, o.w - xo.w);
           *reinterpret_cast<float4*>(z + gi) =
               make_float4(o.x + a.beta * dx.x, o.y + a.beta * dx.y, o.z + a.beta * dx.z, o.w + a.beta * dx.w);
@@ -263,9 +269,12 @@ __host__ __device__ constexpr size_t llr_unit_bytes(int K, int b, int nz) {
 // The K <= 4 float32 variant is held to 80 registers (three CTAs per SM) or, where four
 // CTAs' shared memory fits on an SM, to 64 registers (four per SM; a few values spill to
 // L1), so that the single-thread eigen-steps of one band overlap the memory phases of the
-// others: 0.735 -> 0.649 ms on the knee scan with four.  Where a band is so large that only
-// two CTAs fit (the 12-row bands of Table I's 260 x 240 slices), the CTAs have 512 threads
-// at 64 registers, so the memory phases keep as many loads in flight.
+// others: 0.735 -> 0.649 ms on the knee scan with four.  The FISTA momentum's loads of x_k
+// for a pixel pair are issued for all K images before the row's first store (the compiler
+// may not move a load of x above a store through z, which could alias it): 0.573 -> 0.528
+// ms on the knee scan.  Where a band is so large that only two CTAs fit (the 12-row bands
+// of Table I's 260 x 240 slices), the CTAs have 512 threads at 64 registers, so the memory
+// phases keep as many loads in flight.
 // MODE LLR_PROX: x <- prox(x).  LLR_FISTA: x_{k+1} <- prox(z - mu (grad - aty)),
 // z <- x_{k+1} + beta (x_{k+1} - x_k).  LLR_ADMM: w = x + u (x = alpha), z <- v = prox(w),
 // u <- w - v.
