@@ -108,6 +108,13 @@ def test_workspace_bytes_formula(lib):
     (dict(flags=0x10), t2sh.EINVAL),
     (dict(ny=1024), t2sh.EINVAL),        # above the largest slice matrix, 512
     (dict(block=17), t2sh.EINVAL),       # above the largest block, 16
+    (dict(nslices=0), t2sh.EINVAL),      # an empty batch of slices
+    (dict(nslices=65536), t2sh.EINVAL),  # above the largest batch
+    (dict(ncoils=0), t2sh.EINVAL),
+    (dict(iters=-1), t2sh.EINVAL),
+    (dict(lam=-0.1), t2sh.EINVAL),
+    (dict(lam=float("nan")), t2sh.EINVAL),
+    (dict(step=float("inf")), t2sh.EINVAL),
     # an LLR band of K x b x nz = 4 x 16 x 512 complex values (262 KB) exceeds shared memory
     (dict(ny=512, nz=512, block=16), t2sh.EUNSUPPORTED),
 ])
