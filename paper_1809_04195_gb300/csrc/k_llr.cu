@@ -96,18 +96,20 @@ __device__ __forceinline__ void llr_gather(const Geom& g, const FistaArgs& a, co
     y -= y >= ny ? ny : 0;
     const long long gi = base + (long long)k * N + (long long)y * nz;
     float4 v;
+    // global-space loads (ld.global.cg): the compiler may then batch them across iterations
+    // ahead of the shared-memory stores, which generic loads could alias
     if (MODE == LLR_ADMM) {
-      const float4 av = *reinterpret_cast<const float4*>(x + gi);
-      const float4 uv = *reinterpret_cast<const float4*>(u + gi);
+      const float4 av = __ldcg(reinterpret_cast<const float4*>(x + gi));
+      const float4 uv = __ldcg(reinterpret_cast<const float4*>(u + gi));
       v = make_float4(av.x + uv.x, av.y + uv.y, av.z + uv.z, av.w + uv.w);
     } else if (MODE == LLR_FISTA) {
-      const float4 zv = *reinterpret_cast<const float4*>(z + gi);
-      const float4 gv = *reinterpret_cast<const float4*>(grad + gi);
-      const float4 av = *reinterpret_cast<const float4*>(aty + gi);
+      const float4 zv = __ldcg(reinterpret_cast<const float4*>(z + gi));
+      const float4 gv = __ldcg(reinterpret_cast<const float4*>(grad + gi));
+      const float4 av = __ldcg(reinterpret_cast<const float4*>(aty + gi));
       v = make_float4(zv.x - a.mu * (gv.x - av.x), zv.y - a.mu * (gv.y - av.y), zv.z - a.mu * (gv.z - av.z),
                       zv.w - a.mu * (gv.w - av.w));
     } else {
-      v = *reinterpret_cast<const float4*>(x + gi);
+      v = __ldcg(reinterpret_cast<const float4*>(x + gi));
     }
     *reinterpret_cast<float4*>(gs + (long long)l * llr_ld(nz) + 2 * c.c2) = v;
     r += c.P;
