@@ -32,10 +32,10 @@ using Ex = ExLayout<R1>;
 // two rows (128 threads) and the kernel is held to 64 registers (forward, eight CTAs per
 // SM) or 96 (adjoint, five): many small CTAs keep the SM issuing while others wait at
 // their per-coil barriers (forward 1.47 -> 1.18 ms on the knee scan against bands of 8
-// rows).  N >= 240 and two map sets keep bands of 4 rows without a block bound, except the
-// adjoint with two map sets at N = 240 (Table I), which runs two-row bands at 128 registers
-// (four CTAs per SM): 1.58 -> 1.48 ms (the forward's two-row form spills there: 1.44 ->
-// 2.17 ms).  The
+// rows).  N >= 240 and two map sets keep bands of 4 rows without a block bound, except
+// two map sets at N = 240 (Table I), which run two-row bands at 96 registers for the forward
+// (five CTAs per SM; at 64 registers it spills: 2.17 ms) and 128 for the adjoint (four):
+// forward 1.44 -> 1.39 ms, adjoint 1.58 -> 1.48 ms.  The
 // adjoint reads t straight into registers instead of staging it by cp.async (knee
 // 1.51 -> 1.31 ms, Table I shape 2.30 -> 1.52 ms): the staging cost more instructions
 // than the latency it hid.  On two-row bands the next coil's values are loaded one coil
@@ -58,9 +58,9 @@ struct RowPad {
 template <int N, int MC, int MODE>
 struct RowFastRB {
   // two-row bands, occupancy-bounded kernel
-  static constexpr bool small = (MC == 1 && N < 240) || (MODE == ROW_ADJ && MC == 2 && N == 240);
+  static constexpr bool small = (MC == 1 && N < 240) || (MC == 2 && N == 240);
   static constexpr int value = small ? 2 : 4;
-  static constexpr int min_blocks = MODE == ROW_FWD ? 8 : (MC == 2 ? 4 : 5);
+  static constexpr int min_blocks = MC == 2 ? (MODE == ROW_FWD ? 5 : 4) : (MODE == ROW_FWD ? 8 : 5);
 };
 
 template <int N, int MODE, int MC, int kRowRB = RowFastRB<N, MC, MODE>::value>
