@@ -288,6 +288,47 @@ def test_solve_host_io_pipelined_matches_device(T):
     assert np.allclose(host_res, dev_res, rtol=1e-6, atol=0)
 
 
+def test_plans_made_on_another_thread_during_a_solve(T):
+    """The bench's pipelined host-buffer loop: while one host thread solves scan i through
+    host buffers, another makes scan i+1's host-buffer plan on its own stream.  Every result
+    equals the same solve made one scan after the other, bitwise."""
+    import threading
+    import torch
+    rng, phi, mask, maps = random_problem(47, 16, 64, 48, 4, 16, 4, 1)
+    ys = [(crandn(rng, 16, 4, 4, 64, 48) * 0.05).astype(np.complex64) for _ in range(3)]
+    kw = dict(block=8, lam=0.01, iters=10, seed=6)
+    d = T.make_dims(64, 48, 4, 16, 4, nslices=16, flags=T.HOST_IO, **kw)
+    args = (phi.astype(np.float32), mask.astype(np.uint8), maps.astype(np.complex64))
+    ref = []
+    for y in ys:
+        with T.Plan(d, *args) as p:
+            ref.append(p.solve(y, T.KSPACE_PROJ))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    made, errors = {}, []
+
+    def make(i):
+        try:
+            torch.cuda.set_device(0)
+            made[i] = T.Plan(d, *args, stream=streams[i % 2])
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    got = []
+    worker = threading.Thread(target=make, args=(0,))
+    worker.start()
+    for i, y in enumerate(ys):
+        worker.join()
+        assert not errors, errors
+        p = made.pop(i)
+        if i + 1 < len(ys):
+            worker = threading.Thread(target=make, args=(i + 1,))
+            worker.start()
+        got.append(p.solve(y, T.KSPACE_PROJ))
+        p.close()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
 def test_solve_zero_iterations_and_empty_mask(T):
     rng, phi, mask, maps = random_problem(13, 1, 32, 32, 2, 8, 4, 1)
     zero_mask = np.zeros_like(mask)
