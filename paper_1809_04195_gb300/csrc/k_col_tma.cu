@@ -1,8 +1,8 @@
 // Column pass of the normal operator (DFT_y, Psi, IDFT_y) with its tiles moved by the
 // Tensor Memory Accelerator.  Persistent CTAs walk the (slice, coil, 8-column tile)
-// list; for each tile one thread issues two 3D tensor-map box copies that complete on
-// mbarriers: the K x ny x 8 block of the intermediate t and the P x ny x 8 block of
-// Psi.  The next tile's t block is requested as soon as the forward stage A has read the
+// list; for each tile one thread issues two tensor-map box copies that complete on
+// mbarriers: the K x ny x 8 block of the intermediate t and the (Psi entries) x ny x 8
+// block of Psi.  The next tile's t block is requested as soon as the forward stage A has read the
 // current one.  Once Psi is applied, its block serves as the destination of the inverse
 // stage's transposed lines, so that stage needs no barrier between its reads of the
 // exchange lines and its writes; the next tile's Psi block is requested right after that
@@ -14,7 +14,7 @@
 // inverse [P, R1] two-stage transforms as in the size-specialised kernels.  A half-warp
 // spans the W columns x 16 / W consecutive j of one basis line, the exchange lines are
 // padded to a stride = 16 / W (mod 16) float2 and the in-line layouts use odd strides, so
-// every shared-memory access of the kernel is free of bank conflicts.  A column longer
+// the 16 lanes of a half-warp address 16 different 8-byte bank pairs in every stage.  A column longer
 // than a tensor-map box (256 rows) is copied as two halves by a 4D map whose two middle
 // dimensions split y, landing in the same [k][y][w] layout.  Requires nz % W == 0, K <= 4,
 // ny = N <= 256 or N = 260.
@@ -36,8 +36,8 @@ struct ColTma {
   static constexpr int SI = P + 1;                   // inverse in-line stride (odd)
   static constexpr int LINE = (P * SF > R1 * SI) ? P * SF : R1 * SI;
   static constexpr int THREADS = 4 * W * P;
-  static constexpr int MINB = 8 / W;                             // CTAs per SM the shared memory allows
-  static constexpr bool Y4D = N > 256;                          // y split over two box dimensions
+  static constexpr int MINB = 8 / W;     // CTAs per SM the shared memory allows
+  static constexpr bool Y4D = N > 256;  // y split over two box dimensions
   // a half-warp holds W columns x JPH = 16 / W consecutive j; the exchange line stride
   // LS = JPH (mod 16) with SF = 1 (mod 16) spreads its accesses over all banks
   static constexpr int JPH = 16 / W;
@@ -47,11 +47,12 @@ struct ColTma {
   static constexpr size_t off_psi = off_t + (size_t)4 * N * W * 8;
   // the Psi block also holds the inverse stage's transposed lines once Psi is applied
   static constexpr size_t ex_bytes = (size_t)4 * W * LS * 8;
-  __host__ __device__ static size_t psi_region(int P) {
-    const size_t pb = ((size_t)P * N * W * 4 + 127) / 128 * 128;
+  // np = K (K + 1) / 2 stored entries of Psi per point
+  __host__ __device__ static size_t psi_region(int np) {
+    const size_t pb = ((size_t)np * N * W * 4 + 127) / 128 * 128;
     return pb > ex_bytes ? pb : (ex_bytes + 127) / 128 * 128;
   }
-  __host__ __device__ static size_t smem(int P) { return off_psi + psi_region(P) + 64; }
+  __host__ __device__ static size_t smem(int np) { return off_psi + psi_region(np) + 64; }
 };
 
 // the tile's rows row0 .. row0 + box - 1 of columns z0 .. z0 + W - 1 (3D map, or 4D with y
