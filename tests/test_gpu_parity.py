@@ -362,6 +362,41 @@ def test_solve_knee_slices_projected(T):
         assert e < SOLVE_TOL
 
 
+def test_full_knee_launch_sampled_slices_match_oracle(T):
+    """The knee scan in the launch configuration the bench times: all 320 slices of
+    256 x 160 (C = 12, K = 4) in one plan, 100 FISTA iterations.  Four slices come from the
+    oracle's own seeded inputs; the other 316 are copies of them with maps and k-space at
+    half scale, so the plan's shared step 1 / max_s L_s is set by the four sampled slices
+    (their oracle is given that step).  Slices 0 and 319 against the oracle."""
+    sh = synth.KNEE_320x256x160
+    sl = [0, 101, 160, 319]
+    phi, mask, maps4, ytil4 = proj_scan(sh, sl)
+    phi, maps4 = r32(phi, maps4)
+    S = sh.nslices
+    maps_d = torch.empty((S,) + maps4.shape[1:], dtype=torch.complex64, device="cuda")
+    y_d = torch.empty((S,) + ytil4.shape[1:], dtype=torch.complex64, device="cuda")
+    m4, y4 = c64(maps4), c64(ytil4)
+    for s in range(S):
+        i = sl.index(s) if s in sl else s % 4
+        f = 1.0 if s in sl else 0.5
+        maps_d[s].copy_(m4[i] * f)
+        y_d[s].copy_(y4[i] * f)
+    psi = O.space_time_kernel(mask, phi)
+    mu = 1.0 / max(O.lipschitz(maps4[i], psi) for i in range(4))
+    d = T.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=sh.nmaps, block=sh.block,
+                    lam=sh.lam, iters=sh.iters, seed=sh.seed)
+    with T.Plan(d, dev(phi.astype(np.float32)), dev(mask.astype(np.uint8)), maps_d) as p:
+        assert abs(p.step - mu) <= 1e-5 * mu
+        got = p.solve(y_d, T.KSPACE_PROJ)
+        out = {s: host(got[s]) for s in (sl[0], sl[3])}
+    ys = ytil4.astype(np.complex64).astype(np.complex128)
+    for i in (0, 3):
+        ref = O.fista(ys[i], "proj", maps4[i], mask, phi, sh.lam, sh.block, sh.iters, sh.seed, step=mu)
+        e = nrmse(out[sl[i]], ref)
+        print("full knee launch, slice", sl[i], "NRMSE", e)
+        assert e < SOLVE_TOL
+
+
 def test_solve_paper_shape_slices(T):
     """Two slices of the Table I scan (260 x 240, C = 7, T = 80, K = 4, M = 2 soft-SENSE
     map sets, 12 x 12 LLR blocks, lambda = 0.0125, 1/139 of k-space per echo), projected
