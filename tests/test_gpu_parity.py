@@ -362,38 +362,72 @@ def test_solve_knee_slices_projected(T):
         assert e < SOLVE_TOL
 
 
-def test_full_knee_launch_sampled_slices_match_oracle(T):
+def full_launch(T, sh, sl, **kw):
+    """A whole scan of shape `sh` as one plan (the bench's launch configuration): the listed
+    slices from the oracle's own seeded inputs, every other slice a copy of one of them with
+    maps and k-space at half scale, so that the plan's shared step 1 / max_s L_s is set by
+    the listed slices.  Returns (plan, device k-space, oracle inputs, step)."""
+    phi, mask, maps_l, ytil_l = proj_scan(sh, sl)
+    phi, maps_l = r32(phi, maps_l)
+    S = sh.nslices
+    maps_d = torch.empty((S,) + maps_l.shape[1:], dtype=torch.complex64, device="cuda")
+    y_d = torch.empty((S,) + ytil_l.shape[1:], dtype=torch.complex64, device="cuda")
+    ml, yl = c64(maps_l), c64(ytil_l)
+    for s_ in range(S):
+        i = sl.index(s_) if s_ in sl else s_ % len(sl)
+        f = 1.0 if s_ in sl else 0.5
+        maps_d[s_].copy_(ml[i] * f)
+        y_d[s_].copy_(yl[i] * f)
+    psi = O.space_time_kernel(mask, phi)
+    mu = 1.0 / max(O.lipschitz(maps_l[i], psi) for i in range(len(sl)))
+    d = T.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=sh.nmaps, block=sh.block,
+                    lam=sh.lam, iters=sh.iters, seed=sh.seed, **kw)
+    p = T.Plan(d, dev(phi.astype(np.float32)), dev(mask.astype(np.uint8)), maps_d)
+    assert abs(p.step - mu) <= 1e-5 * mu
+    ys = ytil_l.astype(np.complex64).astype(np.complex128)
+    return p, y_d, (phi, mask, maps_l, ys), mu
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_full_knee_launch_sampled_slices_match_oracle(T, precision):
     """The knee scan in the launch configuration the bench times: all 320 slices of
-    256 x 160 (C = 12, K = 4) in one plan, 100 FISTA iterations.  Four slices come from the
-    oracle's own seeded inputs; the other 316 are copies of them with maps and k-space at
-    half scale, so the plan's shared step 1 / max_s L_s is set by the four sampled slices
-    (their oracle is given that step).  Slices 0 and 319 against the oracle."""
+    256 x 160 (C = 12, K = 4) in one plan, 100 FISTA iterations, in FP32 and with the
+    tensor-core column pass; slices 0 and 319 against the oracle given the plan's step
+    (NRMSE <= 1e-4 in FP32, <= 1e-3 mixed)."""
     sh = synth.KNEE_320x256x160
     sl = [0, 101, 160, 319]
-    phi, mask, maps4, ytil4 = proj_scan(sh, sl)
-    phi, maps4 = r32(phi, maps4)
-    S = sh.nslices
-    maps_d = torch.empty((S,) + maps4.shape[1:], dtype=torch.complex64, device="cuda")
-    y_d = torch.empty((S,) + ytil4.shape[1:], dtype=torch.complex64, device="cuda")
-    m4, y4 = c64(maps4), c64(ytil4)
-    for s in range(S):
-        i = sl.index(s) if s in sl else s % 4
-        f = 1.0 if s in sl else 0.5
-        maps_d[s].copy_(m4[i] * f)
-        y_d[s].copy_(y4[i] * f)
-    psi = O.space_time_kernel(mask, phi)
-    mu = 1.0 / max(O.lipschitz(maps4[i], psi) for i in range(4))
-    d = T.make_dims(sh.ny, sh.nz, sh.ncoils, sh.nechoes, sh.nbasis, nslices=S, nmaps=sh.nmaps, block=sh.block,
-                    lam=sh.lam, iters=sh.iters, seed=sh.seed)
-    with T.Plan(d, dev(phi.astype(np.float32)), dev(mask.astype(np.uint8)), maps_d) as p:
-        assert abs(p.step - mu) <= 1e-5 * mu
+    tol = SOLVE_TOL if precision == "fp32" else 1e-3
+    p, y_d, (phi, mask, maps_l, ys), mu = full_launch(
+        T, sh, sl, precision=T.FP32 if precision == "fp32" else T.MIXED_BF16)
+    with p:
         got = p.solve(y_d, T.KSPACE_PROJ)
-        out = {s: host(got[s]) for s in (sl[0], sl[3])}
-    ys = ytil4.astype(np.complex64).astype(np.complex128)
+        out = {s_: host(got[s_]) for s_ in (sl[0], sl[3])}
     for i in (0, 3):
-        ref = O.fista(ys[i], "proj", maps4[i], mask, phi, sh.lam, sh.block, sh.iters, sh.seed, step=mu)
+        ref = O.fista(ys[i], "proj", maps_l[i], mask, phi, sh.lam, sh.block, sh.iters, sh.seed, step=mu)
         e = nrmse(out[sl[i]], ref)
-        print("full knee launch, slice", sl[i], "NRMSE", e)
+        print(f"full knee launch ({precision}), slice", sl[i], "NRMSE", e)
+        assert e < tol
+
+
+def test_full_batch_of_three_scans_sampled_slices_match_oracle(T):
+    """The batched workload at full size: 320 x 256x160 C = 12, 288 x 240x128 C = 8 and
+    256 x 192x192 C = 16 (100 iterations each) in one batched solve; the last slice of
+    every scan against the oracle given its plan's step."""
+    plans, ks, cases = [], [], []
+    for sh in synth.BATCH_SCANS:
+        sl = [sh.nslices // 2, sh.nslices - 1]
+        p, y_d, case, mu = full_launch(T, sh, sl)
+        plans.append(p)
+        ks.append(y_d)
+        cases.append((sh, sl, case, mu))
+    outs = T.solve_batch(plans, ks)
+    last = [host(o[sh.nslices - 1]) for o, (sh, _, _, _) in zip(outs, cases)]
+    for p in plans:
+        p.close()
+    for got, (sh, sl, (phi, mask, maps_l, ys), mu) in zip(last, cases):
+        ref = O.fista(ys[1], "proj", maps_l[1], mask, phi, sh.lam, sh.block, sh.iters, sh.seed, step=mu)
+        e = nrmse(got, ref)
+        print(f"full batch, {sh.ny}x{sh.nz} C={sh.ncoils} slice {sh.nslices - 1} NRMSE {e:.2e}")
         assert e < SOLVE_TOL
 
 
