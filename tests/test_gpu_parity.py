@@ -88,6 +88,7 @@ SHAPES = [
     (2, 96, 64, 2, 8, 2, 1),     # K = 2 on the specialised passes
     (1, 260, 240, 7, 16, 4, 2),  # Table I slice matrix: radix-13 passes, C = 7, M = 2
     (1, 260, 48, 2, 8, 2, 1),    # 260-point columns (two tensor-map boxes) with K = 2
+    (2, 64, 240, 3, 8, 2, 2),    # two-row row-pass bands for two map sets at nz = 240, K = 2
     (1, 512, 512, 2, 8, 4, 1),   # the largest slice matrix (generic passes)
     (1, 32, 24, 2, 16, 8, 1),    # K = 8, the largest basis
     (2, 8, 8, 1, 4, 2, 1),       # the smallest matrix, one coil
