@@ -29,6 +29,8 @@
  *   - Errors are reported by status code only; nothing is thrown across the ABI.
  *     t2sh_last_error() returns a message for the last failing call of the calling
  *     thread.  A plan is not thread-safe: use one plan per host thread and stream.
+ *     Different plans may be made and used from different host threads at the same
+ *     time (the library's shared state, its memory pool and launch caches, is locked).
  */
 #ifndef T2SH_H
 #define T2SH_H
