@@ -351,6 +351,34 @@ def ncu_traffic(kernel):
     return e.get("dram_bytes_per_launch")
 
 
+def pipelined_steps(make, solve, n):
+    """Run n steps where step i solves the plan from make(i) while make(i + 1) runs on a
+    second host thread.  make(i) returns (plan, seconds spent making it); every plan is
+    closed after its solve.  Returns the summed seconds per phase: plan (on the second
+    thread, overlapped), wait (for a plan to be ready), solve, destroy."""
+    from concurrent.futures import ThreadPoolExecutor
+    t = {"plan": 0.0, "wait": 0.0, "solve": 0.0, "destroy": 0.0}
+    with ThreadPoolExecutor(max_workers=1) as ex:
+        fut = ex.submit(make, 0) if n > 0 else None
+        for i in range(n):
+            t0 = time.perf_counter()
+            p, tp = fut.result()
+            t1 = time.perf_counter()
+            if i + 1 < n:
+                fut = ex.submit(make, i + 1)
+            try:
+                solve(p)
+                t2 = time.perf_counter()
+            finally:
+                p.close()
+            t3 = time.perf_counter()
+            t["plan"] += tp
+            t["wait"] += t1 - t0
+            t["solve"] += t2 - t1
+            t["destroy"] += t3 - t2
+    return t
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -502,7 +530,6 @@ def run_ours(args):
         # pipelined: scan i+1's plan (maps, basis and mask copied from the host, Psi, step) is
         # made on a second host thread and stream while scan i is solved; every scan's host
         # copies still fall inside the timed region
-        from concurrent.futures import ThreadPoolExecutor
         streams = (torch.cuda.Stream(), torch.cuda.Stream())
         pp = {"plan": 0.0, "wait": 0.0, "solve": 0.0, "destroy": 0.0}
 
@@ -513,22 +540,8 @@ def run_ours(args):
             return p, time.perf_counter() - t0
 
         def pipelined(n):
-            with ThreadPoolExecutor(max_workers=1) as ex:
-                fut = ex.submit(make, 0)
-                for i in range(n):
-                    t0 = time.perf_counter()
-                    p, tp = fut.result()
-                    t1 = time.perf_counter()
-                    if i + 1 < n:
-                        fut = ex.submit(make, i + 1)
-                    hsolve(p)
-                    t2 = time.perf_counter()
-                    p.close()
-                    t3 = time.perf_counter()
-                    pp["plan"] += tp
-                    pp["wait"] += t1 - t0
-                    pp["solve"] += t2 - t1
-                    pp["destroy"] += t3 - t2
+            for k, v in pipelined_steps(make, hsolve, n).items():
+                pp[k] += v
 
         pipelined(2)  # warm the second stream and thread
         torch.cuda.synchronize()

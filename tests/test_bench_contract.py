@@ -80,3 +80,61 @@ def test_batch3_config_names_the_three_scans():
     c = bench.batch3_config(1)
     assert c["slices"] == sum(sh.nslices for sh in synth.BATCH_SCANS) == 864
     assert len(c["scans"]) == 3 and "256x160 C=12" in c["workload"] and "192x192 C=16" in c["workload"]
+
+
+class _FakePlan:
+    def __init__(self, i, log):
+        self.i, self.log, self.closed = i, log, False
+
+    def close(self):
+        assert not self.closed
+        self.closed = True
+        self.log.append(("close", self.i))
+
+
+def test_pipelined_steps_overlap_the_next_plan_with_the_solve():
+    """The end-to-end leg's pipelining: plan i+1 is being made on another thread while solve
+    i runs (the solve waits for it to start), every plan is solved once in order and closed
+    after its solve, and the phase times add up."""
+    import threading
+    n = 4
+    log, lock = [], threading.Lock()
+    begun = [threading.Event() for _ in range(n)]
+    threads = {}
+
+    def make(i):
+        begun[i].set()
+        threads[i] = threading.current_thread().ident
+        with lock:
+            log.append(("make", i))
+        return _FakePlan(i, log), 0.001 * (i + 1)
+
+    def solve(p):
+        if p.i + 1 < n:
+            assert begun[p.i + 1].wait(timeout=10), "the next plan was not requested before this solve"
+        with lock:
+            log.append(("solve", p.i))
+
+    t = bench.pipelined_steps(make, solve, n)
+    assert [e[1] for e in log if e[0] == "solve"] == list(range(n))
+    assert [e[1] for e in log if e[0] == "close"] == list(range(n))
+    for i in range(n):
+        assert log.index(("solve", i)) < log.index(("close", i))
+    assert threading.current_thread().ident not in threads.values()
+    assert abs(t["plan"] - 0.010) < 1e-12 and min(t.values()) >= 0
+    assert bench.pipelined_steps(make, solve, 0) == {"plan": 0.0, "wait": 0.0, "solve": 0.0, "destroy": 0.0}
+
+
+def test_pipelined_steps_close_a_plan_whose_solve_fails():
+    log = []
+
+    def make(i):
+        return _FakePlan(i, log), 0.0
+
+    def solve(p):
+        if p.i == 1:
+            raise RuntimeError("solve failed")
+
+    with pytest.raises(RuntimeError):
+        bench.pipelined_steps(make, solve, 3)
+    assert ("close", 0) in log and ("close", 1) in log
